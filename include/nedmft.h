@@ -1,0 +1,237 @@
+/*
+ * nedmft.h -- C ABI of the GB300 nonequilibrium-DMFT lattice-step library.
+ *
+ * Physics (J. K. Freericks, "Quenching Bloch oscillations in a strongly
+ * correlated material", Sec. II): the spinless Falicov-Kimball model at half
+ * filling on the infinite-dimensional hypercubic lattice, in a uniform field
+ * along the diagonal switched on at t = 0, solved on the Kadanoff-Baym-Keldysh
+ * contour discretised into an N_c x N_c complex matrix.
+ *
+ * Conventions shared by every entry point
+ *   - Contour index order: upper real branch (N_t points), lower real branch
+ *     (N_t points), imaginary branch (N_tau points); N_c = 2 N_t + N_tau
+ *     (Eq. time_discrete).  All indices below are 0-based.
+ *   - Matrices are dense, row-major, N_c x N_c, interleaved complex
+ *     (nedmft_c128 == {re, im} == torch.complex128 == C99 double _Complex).
+ *   - A "_d" suffix marks a DEVICE pointer (CUDA global memory of the current
+ *     device); "_host" marks host memory.  The library never frees caller
+ *     memory and never allocates device memory: scratch comes only through an
+ *     explicit workspace whose size a *_workspace_size call returns.  Device
+ *     pointers and the workspace must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     take a stream are stream-ordered and do not synchronise the host unless
+ *     stated; their outputs are ready when the stream reaches them.
+ *   - Return value: 0 (NEDMFT_OK) on success, < 0 on error, > 0 for a
+ *     warning.  No C++ exception crosses this boundary.  On error,
+ *     nedmft_last_error() returns a message for the calling thread.
+ *   - Device-side failures (a pivot below the safety threshold, a bounded
+ *     wait that ran out) are recorded in a device status word that the
+ *     synchronising calls (nedmft_dmft_solve, nedmft_check_status) read back;
+ *     no kernel traps.
+ */
+#ifndef NEDMFT_H
+#define NEDMFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- types */
+
+typedef struct {
+  double re, im;
+} nedmft_c128;
+
+/* The discretised contour (Eqs. time_discrete, integration_weights). */
+typedef struct {
+  double t_min, t_max, dt, beta, dtau;
+  int32_t n_t;   /* points per real branch, (t_max - t_min)/dt */
+  int32_t n_tau; /* imaginary points, beta/dtau */
+  int32_t n_c;   /* 2 n_t + n_tau */
+} nedmft_contour;
+
+/* Falicov-Kimball model in the diagonal field (Eq. hamiltonian_fk,
+ * Eq. vector_potential).  mu = NaN selects half filling, mu = U/2. */
+typedef struct {
+  double U;  /* interaction */
+  double E;  /* field strength, switched on at t = 0 */
+  double w1; /* localized-electron filling <w_1> (1/2 at half filling) */
+  double mu; /* chemical potential, NaN -> U/2 */
+} nedmft_model;
+
+/* Arithmetic of the per-point Dyson solve of nedmft_lattice_gloc. */
+typedef enum {
+  /* FP64 Gauss-Jordan inversion of each B_q - S (DFMA). */
+  NEDMFT_FP64 = 0,
+  /* bf16x3 (hi*hi + hi*lo + lo*hi) tcgen05 tensor-core Gauss-Jordan with
+   * FP32 accumulation in TMEM, then one refinement step whose residual
+   * I - A X is formed with the bidiagonal part in FP64; the sum over q is
+   * FP64. */
+  NEDMFT_MIXED_BF16 = 1,
+  /* the same algorithm with FP32 CUDA-core products (no tensor cores). */
+  NEDMFT_MIXED_FP32 = 2
+} nedmft_precision;
+
+/* ---------------------------------------------------------------- status */
+
+#define NEDMFT_OK 0
+#define NEDMFT_EINVAL (-1)    /* bad argument (message in nedmft_last_error) */
+#define NEDMFT_ENOMEM (-2)    /* workspace smaller than *_workspace_size */
+#define NEDMFT_ECUDA (-3)     /* a CUDA runtime call failed */
+#define NEDMFT_ESINGULAR (-4) /* a Gauss-Jordan pivot fell below the threshold */
+#define NEDMFT_ETIMEOUT (-5)  /* a bounded device wait ran out */
+#define NEDMFT_ENOTCONV 1     /* dmft_solve stopped at max_iter (warning) */
+
+/* Static string for a status code. */
+const char* nedmft_status_string(int status);
+/* Last error message of the calling thread ("" if none). */
+const char* nedmft_last_error(void);
+/* Library version string. */
+const char* nedmft_version(void);
+
+/* Synchronise `stream`, read and clear the device status word (set by the
+ * kernels on a bad pivot or an expired wait).  Returns NEDMFT_OK,
+ * NEDMFT_ESINGULAR or NEDMFT_ETIMEOUT. */
+int nedmft_check_status(void* stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Measurement hooks used by the benchmark (off by default; not for use
+ * while another thread drives the library).  enable != 0 resets and starts
+ * a count of kernel launches; timing != 0 additionally brackets every launch
+ * of the dominant kernel -- the Gauss-Jordan trailing update of the lattice
+ * step -- with CUDA events recorded on its launch stream.  enable = 0 stops
+ * counting. */
+int nedmft_instrument(int enable, int timing);
+
+/* Read the counters: kernel launches since nedmft_instrument(1, .), the
+ * number of timed (trailing-update) launches, their summed event time in
+ * milliseconds, and their summed algorithmic work in real flops
+ * (8 n_c^2 nb per matrix for a rank-nb Gauss-Jordan step, the complex
+ * multiply-add counted as 8 real flops).  Synchronises on the recorded
+ * events.  Any output pointer may be NULL. */
+int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches, double* timed_ms, double* timed_flops);
+
+/* ---------------------------------------------------------------- grid */
+
+/* Contour grid, Sec. II Eqs. time_discrete and integration_weights, with
+ * the first-branch sign fixed by the stated range (t_j = t_min + j dt) and
+ * the imaginary step dtau as a parameter (t = t_min - i dtau k).
+ * Host only.  t_host / w_host (length n_c each) may be NULL for a size
+ * query.  Fails with NEDMFT_EINVAL unless (t_max - t_min)/dt and beta/dtau
+ * are positive integers to within 1e-9 relative. */
+int nedmft_contour_grid(double t_min, double t_max, double dt, double beta,
+                        double dtau, nedmft_contour* out,
+                        nedmft_c128* t_host, nedmft_c128* w_host);
+
+/* Gauss-Hermite rule for the weight exp(-x^2)/sqrt(pi) (Sec. II quadrature
+ * paragraph; Eq. joint_dos), weights summing to 1, nodes ascending.
+ * Host only.  n in [1, 512]. */
+int nedmft_gauss_hermite(int32_t n, double* x_host, double* w_host);
+
+/* Product grid over (eps, ebar), q = a*n + b (eps index outer):
+ * eps[q] = x_a, ebar[q] = x_b, wq[q] = w_a w_b.  Host only, arrays of n*n. */
+int nedmft_quadrature_grid(int32_t n, double* eps_host, double* ebar_host,
+                           double* wq_host);
+
+/* ---------------------------------------------------------------- G0 */
+
+/* Noninteracting contour Green's function of Eq. g_contour_non_final2 for
+ * nq points: g0_d[q][i][j] = G0_{eps_q, ebar_q}(t_i, t_j), with the contour
+ * theta function equal to 1 for i >= j.  eps_d, ebar_d: device, nq doubles.
+ * g0_d: device, nq * n_c * n_c nedmft_c128.  Evaluated in a log-stable form
+ * (every magnitude <= 1).  Stream-ordered. */
+int nedmft_g0_build(const nedmft_contour* c, const nedmft_model* m,
+                    const double* eps_d, const double* ebar_d, int32_t nq,
+                    nedmft_c128* g0_d, void* stream);
+
+/* ---------------------------------------------------------------- lattice */
+
+/* Workspace bytes nedmft_lattice_gloc / nedmft_current need for this contour,
+ * point count and precision.  `batch` = points solved concurrently
+ * (0 = library default for n_c).  Returns 0 on a bad argument. */
+size_t nedmft_lattice_workspace_size(const nedmft_contour* c, int32_t nq,
+                                     nedmft_precision prec, int32_t batch);
+
+/* The lattice step (Eq. g_loc and Eq. current_def):
+ *   gloc = sum_q wq[q] G_q,   G_q = [(I - G0_q S)^-1 G0_q] = (B_q - S)^-1,
+ *   S = W Sigma W (Eq. matrix_multiply), B_q = G0_q^-1 (bidiagonal + one
+ *   boundary element, built in closed form),
+ *   j[m]      = Re[ i sum_q wq[q] ebar_q(t_m) G_q[m][2 N_t - m] ],
+ *   j_imag[m] = Im[ same ]      (vanishes for the exact solution),
+ * for the upper-branch times t_m = t_min + m dt, m = 0..N_t-1, with
+ * ebar_q(t) = ebar cos(Et) + eps sin(Et) for t > 0, ebar otherwise.
+ * Points are summed in ascending q in FP64, so the result is deterministic.
+ *   sigma_d: device, n_c x n_c self-energy Sigma(t_i, t_j).
+ *   eps_d, ebar_d, wq_d: device, nq doubles each.
+ *   gloc_d: device, n_c x n_c output (overwritten).
+ *   j_d, j_imag_d: device, n_t doubles each, or NULL to skip.
+ *   ws_d / ws_bytes: workspace of at least
+ *     nedmft_lattice_workspace_size(c, nq, prec, batch) bytes, where batch is
+ *     the value of the environment-free default (0).
+ * Stream-ordered; no host synchronisation. */
+int nedmft_lattice_gloc(const nedmft_contour* c, const nedmft_model* m,
+                        const nedmft_c128* sigma_d, const double* eps_d,
+                        const double* ebar_d, const double* wq_d, int32_t nq,
+                        nedmft_precision prec, nedmft_c128* gloc_d,
+                        double* j_d, double* j_imag_d, void* ws_d,
+                        size_t ws_bytes, void* stream);
+
+/* The current alone (Eq. current_def): one lattice pass whose G_loc stays in
+ * the workspace.  Same arguments and workspace as nedmft_lattice_gloc. */
+int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
+                   const nedmft_c128* sigma_d, const double* eps_d,
+                   const double* ebar_d, const double* wq_d, int32_t nq,
+                   nedmft_precision prec, double* j_d, double* j_imag_d,
+                   void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- impurity */
+
+/* Workspace bytes for nedmft_impurity_update. */
+size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
+
+/* One Falicov-Kimball impurity step in FP64 (Eqs. effective_medium,
+ * dynamical_mean_field, g_imp_solve; the M matrix of the discretised
+ * (i d/dt + mu) delta_c; the operator inverse of Eq.
+ * matrix_inverse_discrete):
+ *   A0 = inv(G_loc) + S,  A1 = A0 + i [M(mu - U) - M(mu)],
+ *   G_imp = (1 - w1) inv(A0) + w1 inv(A1),
+ *   sigma_new = W^-1 (A0 - inv(G_imp)) W^-1.
+ * Inversions: Gauss-Jordan with partial pivoting.  gimp_d may be NULL.
+ * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered. */
+int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
+                           const nedmft_c128* gloc_d,
+                           const nedmft_c128* sigma_d,
+                           nedmft_c128* sigma_new_d, nedmft_c128* gimp_d,
+                           void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- loop */
+
+/* Workspace bytes for nedmft_dmft_solve. */
+size_t nedmft_dmft_workspace_size(const nedmft_contour* c, int32_t n_quad,
+                                  nedmft_precision prec);
+
+/* The DMFT loop of Sec. II on an n_quad x n_quad Gauss-Hermite grid:
+ * lattice step, convergence test max|G_new - G_old| / max|G_new| < tol,
+ * impurity step, Sigma <- Sigma_new (no mixing).  Sigma starts at
+ * sigma_init_d (device, n_c x n_c) or at 0 if it is NULL.
+ * Outputs (device): sigma_d (the Sigma that produced the returned G_loc),
+ * gloc_d, j_d (n_t doubles, or NULL).  Host outputs: *iters (lattice steps
+ * taken), *err (last convergence error).  Synchronises `stream` once per
+ * iteration (one scalar read).  Returns NEDMFT_ENOTCONV if max_iter lattice
+ * steps did not converge. */
+int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
+                      int32_t n_quad, nedmft_precision prec,
+                      const nedmft_c128* sigma_init_d, double tol,
+                      int32_t max_iter, nedmft_c128* sigma_d,
+                      nedmft_c128* gloc_d, double* j_d, int32_t* iters,
+                      double* err, void* ws_d, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEDMFT_H */

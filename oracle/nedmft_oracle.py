@@ -335,7 +335,9 @@ def dmft_solve(c: Contour, model: Model, n_quad: int, tol: float = 1e-8,
 
     Iteration k computes G_loc from Sigma_k; once two successive G_loc agree to
     ``tol`` the loop stops and returns that G_loc, its current and the Sigma it
-    came from.  Otherwise Sigma_{k+1} = impurity(G_loc, Sigma_k).
+    came from.  Otherwise Sigma_{k+1} = impurity(G_loc, Sigma_k).  After
+    ``max_iter`` lattice steps without convergence the last G_loc and the Sigma
+    that produced it are returned.
     """
     eps, ebar, wq = quadrature_points(n_quad)
     sigma = np.zeros((c.n_c, c.n_c), np.complex128) if sigma0 is None else sigma0.copy()
@@ -347,6 +349,8 @@ def dmft_solve(c: Contour, model: Model, n_quad: int, tol: float = 1e-8,
             err = convergence_error(gloc, g_old)
             if err < tol:
                 return DmftResult(sigma, gloc, jc, it, err, True)
+        if it == max_iter:
+            break
         g_old = gloc
         sigma, _ = impurity_update(c, model, gloc, sigma)
     return DmftResult(sigma, gloc, jc, max_iter, err, False)

@@ -1,0 +1,229 @@
+// C-ABI entry points of the lattice step, the G0 builder and the DMFT loop.
+#include <math.h>
+
+#include <vector>
+
+#include "lattice.cuh"
+#include "umma.cuh"
+
+namespace nedmft {
+
+namespace {
+
+constexpr int kNbSimt = 32;  // Gauss-Jordan block of the CUDA-core path
+
+int padded(int n) { return ((n + 127) / 128) * 128; }
+
+bool valid_contour(const nedmft_contour* c) {
+  return c && c->n_t >= 1 && c->n_tau >= 1 && c->n_c == 2 * c->n_t + c->n_tau && c->dt > 0 && c->dtau > 0 &&
+         c->beta > 0 && c->n_c <= 65536;
+}
+
+ModelDev model_dev(const nedmft_model& m) { return ModelDev{m.U, m.E, m.w1, isnan(m.mu) ? m.U / 2 : m.mu}; }
+
+enum class Path { Small64, Blocked64, MixedSimt, MixedUmma };
+
+Path choose_path(const nedmft_contour& c, nedmft_precision p) {
+  if (p == NEDMFT_FP64) return c.n_c <= small_path_max_n() ? Path::Small64 : Path::Blocked64;
+  if (p == NEDMFT_MIXED_FP32) return Path::MixedSimt;
+  return Path::MixedUmma;
+}
+
+int default_batch(const nedmft_contour& c, int nq, Path path) {
+  const size_t np = padded(c.n_c);
+  size_t per = 0, budget = (size_t)8 << 30;  // about 8 GB of batch buffers
+  int cap = 152;
+  switch (path) {
+    case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
+    case Path::Blocked64: per = sizeof(double2) * np * np; cap = 152; break;
+    case Path::MixedSimt: per = 3 * sizeof(float2) * np * np; cap = 64; break;
+    case Path::MixedUmma: per = umma_batch_bytes_per_matrix((int)np); cap = umma_default_batch((int)np); break;
+  }
+  int b = (int)(budget / (per ? per : 1));
+  if (b > cap) b = cap;
+  if (b > nq) b = nq;
+  if (b < 1) b = 1;
+  return b;
+}
+
+struct LatticeLayout {
+  size_t S, gscratch, jacc, batch, pbuf, rbuf, cbuf, extra, total;
+  int np, mb;
+  Path path;
+};
+
+LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision prec, int batch) {
+  LatticeLayout L{};
+  L.path = choose_path(c, prec);
+  L.np = padded(c.n_c);
+  L.mb = batch > 0 ? (batch < nq ? batch : nq) : default_batch(c, nq, L.path);
+  const size_t n = c.n_c, np = L.np, mb = L.mb;
+  L.S = align256(sizeof(double2) * n * n);
+  L.gscratch = align256(sizeof(double2) * n * n);
+  L.jacc = align256(sizeof(double2) * c.n_t);
+  switch (L.path) {
+    case Path::Small64:
+      L.batch = align256(sizeof(double2) * n * n * mb);
+      break;
+    case Path::Blocked64:
+      L.batch = align256(sizeof(double2) * np * np * mb);
+      L.pbuf = align256(sizeof(double2) * kNbSimt * kNbSimt * mb);
+      L.rbuf = align256(sizeof(double2) * kNbSimt * np * mb);
+      L.cbuf = align256(sizeof(double2) * np * kNbSimt * mb);
+      break;
+    case Path::MixedSimt:
+      L.batch = 3 * align256(sizeof(float2) * np * np * mb);  // X', T / dX', R'
+      L.pbuf = align256(sizeof(float2) * kNbSimt * kNbSimt * mb);
+      L.rbuf = align256(sizeof(float2) * kNbSimt * np * mb);
+      L.cbuf = align256(sizeof(float2) * np * kNbSimt * mb);
+      L.extra = align256(sizeof(float2) * np * np);  // S in FP32, padded
+      break;
+    case Path::MixedUmma:
+      L.batch = align256(umma_batch_bytes_per_matrix((int)np) * mb);
+      L.extra = align256(umma_shared_bytes((int)np));
+      break;
+  }
+  L.total = L.S + L.gscratch + L.jacc + L.batch + L.pbuf + L.rbuf + L.cbuf + L.extra + 256;
+  return L;
+}
+
+}  // namespace
+
+// The lattice step proper (also used by the current and the DMFT loop).
+int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
+                const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
+                double* ji, void* ws, size_t ws_bytes, cudaStream_t st) {
+  LatticeLayout L = lattice_layout(c, nq, prec, 0);
+  if (ws_bytes < L.total) return set_error(NEDMFT_ENOMEM, "lattice: workspace %zu < %zu bytes", ws_bytes, L.total);
+  int* status = device_status_ptr();
+  if (!status) return set_error(NEDMFT_ECUDA, "lattice: no device status word");
+  const ContourDev cd = to_dev(c);
+  const ModelDev md = model_dev(m);
+  char* p = static_cast<char*>(ws);
+  double2* S = reinterpret_cast<double2*>(p); p += L.S;
+  double2* gs = reinterpret_cast<double2*>(p); p += L.gscratch;
+  double2* jacc = reinterpret_cast<double2*>(p); p += L.jacc;
+  char* batch = p; p += L.batch;
+  char* pbuf = p; p += L.pbuf;
+  char* rbuf = p; p += L.rbuf;
+  char* cbuf = p; p += L.cbuf;
+  char* extra = p;
+  if (!gloc) gloc = gs;
+  double2* ja = (j || ji) ? jacc : nullptr;
+  const int np = L.np, mb = L.mb;
+  int rc = launch_build_s(cd, sigma, S, st);
+  if (rc) return rc;
+  if (L.path == Path::MixedSimt) {
+    if ((rc = launch_to_f32_padded(S, cd.n, reinterpret_cast<float2*>(extra), np, st))) return rc;
+  }
+  if (L.path == Path::MixedUmma) {
+    if ((rc = umma_prepare_shared(cd, S, np, extra, st))) return rc;
+  }
+  for (int q0 = 0; q0 < nq; q0 += mb) {
+    const int nb = (nq - q0) < mb ? (nq - q0) : mb;
+    const bool first = (q0 == 0);
+    switch (L.path) {
+      case Path::Small64: {
+        double2* out = reinterpret_cast<double2*>(batch);
+        if ((rc = launch_gj_small_fp64(cd, md, eps, ebar, q0, nb, S, out, status, st))) return rc;
+        if ((rc = launch_reduce<double>(cd, md, eps, ebar, wq, q0, nb, out, nullptr, cd.n, false, first, gloc, ja, st)))
+          return rc;
+        break;
+      }
+      case Path::Blocked64: {
+        double2* A = reinterpret_cast<double2*>(batch);
+        if ((rc = launch_gen_a<double>(cd, md, eps, ebar, q0, nb, S, A, np, st))) return rc;
+        if ((rc = gj_blocked_simt<double>(A, cd.n, np, nb, reinterpret_cast<double2*>(pbuf), reinterpret_cast<double2*>(rbuf),
+                                          reinterpret_cast<double2*>(cbuf), status, st)))
+          return rc;
+        if ((rc = launch_reduce<double>(cd, md, eps, ebar, wq, q0, nb, A, nullptr, np, true, first, gloc, ja, st)))
+          return rc;
+        break;
+      }
+      case Path::MixedSimt: {
+        const size_t one = align256(sizeof(float2) * (size_t)np * np * mb);
+        float2* X = reinterpret_cast<float2*>(batch);
+        float2* T = reinterpret_cast<float2*>(batch + one);
+        float2* R = reinterpret_cast<float2*>(batch + 2 * one);
+        const size_t mat = (size_t)np * np;
+        if ((rc = launch_gen_a<float>(cd, md, eps, ebar, q0, nb, S, X, np, st))) return rc;
+        if ((rc = gj_blocked_simt<float>(X, cd.n, np, nb, reinterpret_cast<float2*>(pbuf), reinterpret_cast<float2*>(rbuf),
+                                         reinterpret_cast<float2*>(cbuf), status, st)))
+          return rc;
+        // T = S X' (shared S), R' = I - A' X', dX' = X' R'
+        if ((rc = gemm_simt<float>(reinterpret_cast<const float2*>(extra), np, 0, X, np, mat, T, np, mat, np, np, np, nb,
+                                   st)))
+          return rc;
+        if ((rc = launch_residual<float>(cd, md, eps, ebar, q0, nb, X, T, np, mat, R, np, st))) return rc;
+        if ((rc = gemm_simt<float>(X, np, mat, R, np, mat, T, np, mat, np, np, np, nb, st))) return rc;
+        if ((rc = launch_reduce<float>(cd, md, eps, ebar, wq, q0, nb, X, T, np, true, first, gloc, ja, st))) return rc;
+        break;
+      }
+      case Path::MixedUmma: {
+        if ((rc = umma_lattice_batch(cd, md, eps, ebar, wq, q0, nb, np, S, extra, batch, first, gloc, ja, status, st)))
+          return rc;
+        break;
+      }
+    }
+  }
+  if (ja) {
+    if ((rc = launch_finish_current(cd.nt, jacc, j, ji, st))) return rc;
+  }
+  return NEDMFT_OK;
+}
+
+}  // namespace nedmft
+
+using namespace nedmft;
+
+extern "C" int nedmft_g0_build(const nedmft_contour* c, const nedmft_model* m, const double* eps_d,
+                               const double* ebar_d, int32_t nq, nedmft_c128* g0_d, void* stream) {
+  if (!valid_contour(c)) return set_error(NEDMFT_EINVAL, "g0_build: invalid contour");
+  if (!m || !eps_d || !ebar_d || !g0_d) return set_error(NEDMFT_EINVAL, "g0_build: NULL argument");
+  if (nq < 1 || nq > 65535) return set_error(NEDMFT_EINVAL, "g0_build: nq = %d outside [1, 65535]", nq);
+  return launch_g0_build(to_dev(*c), model_dev(*m), eps_d, ebar_d, nq, reinterpret_cast<double2*>(g0_d),
+                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t nedmft_lattice_workspace_size(const nedmft_contour* c, int32_t nq, nedmft_precision prec,
+                                                int32_t batch) {
+  if (!valid_contour(c) || nq < 1) return 0;
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32) return 0;
+  return lattice_layout(*c, nq, prec, batch).total;
+}
+
+static int lattice_checks(const nedmft_contour* c, const nedmft_model* m, const void* sigma, const double* eps,
+                          const double* ebar, const double* wq, int nq, nedmft_precision prec, void* ws) {
+  if (!valid_contour(c)) return set_error(NEDMFT_EINVAL, "lattice: invalid contour");
+  if (!m) return set_error(NEDMFT_EINVAL, "lattice: model is NULL");
+  if (!sigma || !eps || !ebar || !wq || !ws) return set_error(NEDMFT_EINVAL, "lattice: NULL device pointer");
+  if (nq < 1) return set_error(NEDMFT_EINVAL, "lattice: nq = %d < 1", nq);
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32)
+    return set_error(NEDMFT_EINVAL, "lattice: unknown precision %d", (int)prec);
+  if (((uintptr_t)ws) & 255) return set_error(NEDMFT_EINVAL, "lattice: workspace not 256-byte aligned");
+  if (!(m->w1 >= 0.0 && m->w1 <= 1.0)) return set_error(NEDMFT_EINVAL, "lattice: w1 = %g outside [0, 1]", m->w1);
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_lattice_gloc(const nedmft_contour* c, const nedmft_model* m, const nedmft_c128* sigma_d,
+                                   const double* eps_d, const double* ebar_d, const double* wq_d, int32_t nq,
+                                   nedmft_precision prec, nedmft_c128* gloc_d, double* j_d, double* j_imag_d,
+                                   void* ws_d, size_t ws_bytes, void* stream) {
+  int rc = lattice_checks(c, m, sigma_d, eps_d, ebar_d, wq_d, nq, prec, ws_d);
+  if (rc) return rc;
+  if (!gloc_d) return set_error(NEDMFT_EINVAL, "lattice_gloc: gloc_d is NULL");
+  return lattice_run(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec,
+                     reinterpret_cast<double2*>(gloc_d), j_d, j_imag_d, ws_d, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int nedmft_current(const nedmft_contour* c, const nedmft_model* m, const nedmft_c128* sigma_d,
+                              const double* eps_d, const double* ebar_d, const double* wq_d, int32_t nq,
+                              nedmft_precision prec, double* j_d, double* j_imag_d, void* ws_d, size_t ws_bytes,
+                              void* stream) {
+  int rc = lattice_checks(c, m, sigma_d, eps_d, ebar_d, wq_d, nq, prec, ws_d);
+  if (rc) return rc;
+  if (!j_d && !j_imag_d) return set_error(NEDMFT_EINVAL, "current: both outputs NULL");
+  return lattice_run(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec, nullptr, j_d,
+                     j_imag_d, ws_d, ws_bytes, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,162 @@
+// The DMFT self-consistency loop of Sec. II on the device.
+#include <math.h>
+
+#include <vector>
+
+#include "lattice.cuh"
+
+namespace nedmft {
+
+int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
+                const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
+                double* ji, void* ws, size_t ws_bytes, cudaStream_t st);
+
+namespace {
+
+constexpr int kNormBlocks = 304;
+
+// Per-block maxima of |a - b| and |a| (pass 1) and their global maxima (pass 2):
+// err = max|a - b| / max|a|, deterministic.
+__global__ void norm_pass1(const double2* __restrict__ a, const double2* __restrict__ b, size_t total,
+                           double* __restrict__ part) {
+  __shared__ double sd[256], sa[256];
+  double md = 0.0, ma = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    double2 x = a[e], y = b[e];
+    double dx = x.x - y.x, dy = x.y - y.y;
+    md = fmax(md, sqrt(dx * dx + dy * dy));
+    ma = fmax(ma, sqrt(x.x * x.x + x.y * x.y));
+  }
+  sd[threadIdx.x] = md;
+  sa[threadIdx.x] = ma;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+      sa[threadIdx.x] = fmax(sa[threadIdx.x], sa[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sd[0];
+    part[2 * blockIdx.x + 1] = sa[0];
+  }
+}
+
+__global__ void norm_pass2(const double* __restrict__ part, int nblocks, double* __restrict__ err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double md = 0.0, ma = 0.0;
+  for (int i = 0; i < nblocks; ++i) {
+    md = fmax(md, part[2 * i]);
+    ma = fmax(ma, part[2 * i + 1]);
+  }
+  *err = ma > 0.0 ? md / ma : (md > 0.0 ? INFINITY : 0.0);
+}
+
+struct DmftLayout {
+  size_t quad, gbuf, sbuf, part, lat, imp, total;
+};
+
+DmftLayout dmft_layout(const nedmft_contour& c, int n_quad, nedmft_precision prec) {
+  DmftLayout L{};
+  const size_t n = c.n_c, nq = (size_t)n_quad * n_quad;
+  L.quad = 3 * align256(sizeof(double) * nq);
+  L.gbuf = 2 * align256(sizeof(double2) * n * n);
+  L.sbuf = 2 * align256(sizeof(double2) * n * n);
+  L.part = align256(sizeof(double) * (2 * kNormBlocks + 1));
+  L.lat = align256(nedmft_lattice_workspace_size(&c, (int)nq, prec, 0));
+  L.imp = align256(nedmft_impurity_workspace_size(&c));
+  L.total = L.quad + L.gbuf + L.sbuf + L.part + L.lat + L.imp + 256;
+  return L;
+}
+
+}  // namespace
+}  // namespace nedmft
+
+using namespace nedmft;
+
+extern "C" size_t nedmft_dmft_workspace_size(const nedmft_contour* c, int32_t n_quad, nedmft_precision prec) {
+  if (!c || n_quad < 1 || n_quad > 512 || c->n_c < 2) return 0;
+  if (nedmft_lattice_workspace_size(c, n_quad * n_quad, prec, 0) == 0) return 0;
+  return dmft_layout(*c, n_quad, prec).total;
+}
+
+extern "C" int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m, int32_t n_quad,
+                                 nedmft_precision prec, const nedmft_c128* sigma_init_d, double tol, int32_t max_iter,
+                                 nedmft_c128* sigma_d, nedmft_c128* gloc_d, double* j_d, int32_t* iters, double* err,
+                                 void* ws_d, size_t ws_bytes, void* stream) {
+  if (!c || !m || !sigma_d || !gloc_d || !ws_d) return set_error(NEDMFT_EINVAL, "dmft_solve: NULL argument");
+  if (n_quad < 1 || n_quad > 512) return set_error(NEDMFT_EINVAL, "dmft_solve: n_quad = %d outside [1, 512]", n_quad);
+  if (max_iter < 1) return set_error(NEDMFT_EINVAL, "dmft_solve: max_iter < 1");
+  if (!(tol > 0.0)) return set_error(NEDMFT_EINVAL, "dmft_solve: tol must be > 0");
+  const size_t need = nedmft_dmft_workspace_size(c, n_quad, prec);
+  if (need == 0) return set_error(NEDMFT_EINVAL, "dmft_solve: invalid contour or precision");
+  if (ws_bytes < need) return set_error(NEDMFT_ENOMEM, "dmft_solve: workspace %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws_d) & 255) return set_error(NEDMFT_EINVAL, "dmft_solve: workspace not 256-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DmftLayout L = dmft_layout(*c, n_quad, prec);
+  const int nq = n_quad * n_quad;
+  const size_t n = c->n_c, nn = n * n;
+  char* p = static_cast<char*>(ws_d);
+  double* eps = reinterpret_cast<double*>(p);
+  double* ebar = reinterpret_cast<double*>(p + align256(sizeof(double) * nq));
+  double* wq = reinterpret_cast<double*>(p + 2 * align256(sizeof(double) * nq));
+  p += L.quad;
+  double2* g[2] = {reinterpret_cast<double2*>(p), reinterpret_cast<double2*>(p + align256(sizeof(double2) * nn))};
+  p += L.gbuf;
+  double2* s[2] = {reinterpret_cast<double2*>(p), reinterpret_cast<double2*>(p + align256(sizeof(double2) * nn))};
+  p += L.sbuf;
+  double* part = reinterpret_cast<double*>(p);
+  double* err_d = part + 2 * kNormBlocks;
+  p += L.part;
+  void* lat_ws = p;
+  p += L.lat;
+  void* imp_ws = p;
+
+  std::vector<double> he(nq), hb(nq), hw(nq);
+  int rc = nedmft_quadrature_grid(n_quad, he.data(), hb.data(), hw.data());
+  if (rc) return rc;
+  NED_CUDA(cudaMemcpyAsync(eps, he.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaMemcpyAsync(ebar, hb.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaMemcpyAsync(wq, hw.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  if (sigma_init_d)
+    NED_CUDA(cudaMemcpyAsync(s[0], sigma_init_d, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+  else
+    NED_CUDA(cudaMemsetAsync(s[0], 0, sizeof(double2) * nn, st));
+
+  int cur = 0, gcur = 0;
+  double e_host = INFINITY;
+  int it = 0;
+  bool conv = false;
+  for (it = 1; it <= max_iter; ++it) {
+    rc = lattice_run(*c, *m, s[cur], eps, ebar, wq, nq, prec, g[gcur], j_d, nullptr, lat_ws, L.lat, st);
+    if (rc) return rc;
+    if (it > 1) {
+      norm_pass1<<<kNormBlocks, 256, 0, st>>>(g[gcur], g[1 - gcur], nn, part);
+      NED_LAUNCH_CHECK("norm_pass1");
+      norm_pass2<<<1, 32, 0, st>>>(part, kNormBlocks, err_d);
+      NED_LAUNCH_CHECK("norm_pass2");
+      NED_CUDA(cudaMemcpyAsync(&e_host, err_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NED_CUDA(cudaStreamSynchronize(st));
+      int ds = nedmft_check_status(stream);
+      if (ds) return ds;
+      if (e_host < tol) { conv = true; break; }
+    }
+    if (it == max_iter) break;
+    rc = nedmft_impurity_update(c, m, reinterpret_cast<const nedmft_c128*>(g[gcur]),
+                                reinterpret_cast<const nedmft_c128*>(s[cur]), reinterpret_cast<nedmft_c128*>(s[1 - cur]),
+                                nullptr, imp_ws, L.imp, stream);
+    if (rc) return rc;
+    cur = 1 - cur;
+    gcur = 1 - gcur;
+  }
+  if (it > max_iter) it = max_iter;
+  NED_CUDA(cudaMemcpyAsync(gloc_d, g[gcur], sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+  NED_CUDA(cudaMemcpyAsync(sigma_d, s[cur], sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
+  NED_CUDA(cudaStreamSynchronize(st));
+  int ds = nedmft_check_status(stream);
+  if (ds) return ds;
+  if (iters) *iters = it;
+  if (err) *err = e_host;
+  return conv ? NEDMFT_OK : NEDMFT_ENOTCONV;
+}

@@ -1,0 +1,555 @@
+// CUDA-core kernels of the lattice step: S = W Sigma W, the fused B_q - S
+// generator, the dense G0 builder, Gauss-Jordan inversion (single-CTA for
+// small N_c, blocked and batched for large N_c), the refinement residual and
+// the FP64 quadrature / current reductions.
+#include "lattice.cuh"
+
+namespace nedmft {
+
+// ------------------------------------------------------------------ S = W Sigma W
+
+__global__ void build_s_kernel(ContourDev c, const double2* __restrict__ sigma, double2* __restrict__ S) {
+  size_t total = (size_t)c.n * c.n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / c.n), j = (int)(e % c.n);
+    S[e] = cmul(cmul(weight(c, i), sigma[e]), weight(c, j));
+  }
+}
+
+int launch_build_s(const ContourDev& c, const double2* sigma, double2* S, cudaStream_t st) {
+  size_t total = (size_t)c.n * c.n;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  build_s_kernel<<<blocks, 256, 0, st>>>(c, sigma, S);
+  NED_LAUNCH_CHECK("build_s_kernel");
+  return NEDMFT_OK;
+}
+
+// ------------------------------------------------------------------ G0 (dense)
+
+// G0(t_i, t_j) of Eq. g_contour_non_final2 in the log-stable form:
+//   i >= j: -i exp(-x (tau_i - tau_j) - softplus(-beta x)) e^{i phase},
+//   i <  j:  i exp(-x (tau_i - tau_j) - softplus( beta x)) e^{i phase},
+// phase = mu Re(t_i - t_j) - [F(t_i) - F(t_j)].
+__global__ void g0_build_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                const double* __restrict__ ebar_d, double2* __restrict__ g0) {
+  const int q = blockIdx.y;
+  const double eps = eps_d[q], ebar = ebar_d[q];
+  const double x = eps - m.mu;
+  const double sp_neg = x > 0 ? log1p(exp(-c.beta * x)) : -c.beta * x + log1p(exp(c.beta * x));   // softplus(-beta x)
+  const double sp_pos = x > 0 ? c.beta * x + log1p(exp(-c.beta * x)) : log1p(exp(c.beta * x));    // softplus(beta x)
+  size_t total = (size_t)c.n * c.n;
+  double2* out = g0 + (size_t)q * total;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / c.n), j = (int)(e % c.n);
+    double si = t_re(c, i), sj = t_re(c, j);
+    double ph = m.mu * (si - sj) - band_phase_diff(sj, si, eps, ebar, m.E);
+    double re = -x * (t_tau(c, i) - t_tau(c, j));
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    double mag, pre;
+    if (i >= j) { mag = exp(re - sp_neg); pre = -1.0; } else { mag = exp(re - sp_pos); pre = 1.0; }
+    // pre * i * mag * (cs + i sn) = pre * mag * (-sn + i cs)
+    out[e] = make_double2(-pre * mag * sn, pre * mag * cs);
+  }
+}
+
+int launch_g0_build(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int nq,
+                    double2* g0, cudaStream_t st) {
+  size_t total = (size_t)c.n * c.n;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 1024) bx = 1024;
+  dim3 grid(bx, nq);
+  g0_build_kernel<<<grid, 256, 0, st>>>(c, m, eps, ebar, g0);
+  NED_LAUNCH_CHECK("g0_build_kernel");
+  return NEDMFT_OK;
+}
+
+// ------------------------------------------------------------------ A'_q = P (B_q - S), padded
+
+template <class T>
+__global__ void gen_a_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                             const double* __restrict__ ebar_d, int q0, const double2* __restrict__ S,
+                             cplx_t<T>* __restrict__ A, int np) {
+  const int b = blockIdx.y;
+  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+  const bool sh = shifted_point(m, eps);
+  const size_t total = (size_t)np * np;
+  cplx_t<T>* out = A + (size_t)b * total;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(e / np), col = (int)(e % np);
+    double2 v;
+    if (r < c.n && col < c.n) {
+      int i = sh ? (r + 1 == c.n ? 0 : r + 1) : r;
+      v = a_entry(c, m, eps, ebar, S, i, col);
+    } else {
+      v = make_double2(r == col ? 1.0 : 0.0, 0.0);
+    }
+    out[e] = cvt<T>(v);
+  }
+}
+
+template <class T>
+int launch_gen_a(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0, int nb,
+                 const double2* S, cplx_t<T>* A, int np, cudaStream_t st) {
+  size_t total = (size_t)np * np;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 4096) bx = 4096;
+  dim3 grid(bx, nb);
+  gen_a_kernel<T><<<grid, 256, 0, st>>>(c, m, eps, ebar, q0, S, A, np);
+  NED_LAUNCH_CHECK("gen_a_kernel");
+  return NEDMFT_OK;
+}
+template int launch_gen_a<double>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
+                                  const double2*, double2*, int, cudaStream_t);
+template int launch_gen_a<float>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
+                                 const double2*, float2*, int, cudaStream_t);
+
+// ------------------------------------------------------------------ record a device failure
+
+__device__ __forceinline__ void record_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ in-shared-memory Gauss-Jordan
+
+// In-place inverse of the n x n matrix `a` (row stride ld) held in shared
+// memory, no pivoting (the static row order makes the pivots safe), all
+// threads of the block participating.  `col` is n scratch entries.
+template <class T>
+__device__ void smem_gauss_jordan(cplx_t<T>* a, int n, int ld, cplx_t<T>* col, T tiny, int* status) {
+  using C = cplx_t<T>;
+  for (int k = 0; k < n; ++k) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) col[t] = a[t * ld + k];
+    __syncthreads();
+    C pinv;
+    bool ok = cinv_guard<T>(col[k], pinv, tiny);
+    if (!ok && threadIdx.x == 0) record_status(status, DS_SINGULAR);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) a[k * ld + t] = (t == k) ? pinv : cmul(a[k * ld + t], pinv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, j = e % n;
+      if (i == k) continue;
+      C f = col[i];
+      if (j == k) {
+        C v = cmul(f, pinv);
+        a[i * ld + k] = mk<T>(-v.x, -v.y);
+      } else {
+        C v = a[i * ld + j];
+        C r = a[k * ld + j];
+        v.x -= f.x * r.x - f.y * r.y;
+        v.y -= f.x * r.y + f.y * r.x;
+        a[i * ld + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Small N_c: one CTA per point generates A'_q in shared memory, inverts it
+// and writes G_q (columns un-cycled) in FP64 to out[b].
+__global__ void __launch_bounds__(512) gj_small_fp64_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                                            const double* __restrict__ ebar_d, int q0,
+                                                            const double2* __restrict__ S, double2* __restrict__ out,
+                                                            int* status) {
+  extern __shared__ double2 sm[];
+  const int n = c.n, b = blockIdx.x;
+  double2* a = sm;
+  double2* col = sm + n * n;
+  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+  const bool sh = shifted_point(m, eps);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, j = e % n;
+    int i = sh ? (r + 1 == n ? 0 : r + 1) : r;
+    a[e] = a_entry(c, m, eps, ebar, S, i, j);
+  }
+  __syncthreads();
+  smem_gauss_jordan<double>(a, n, n, col, 1e-12, status);
+  double2* o = out + (size_t)b * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e % n;
+    o[e] = a[i * n + unshift_col(j, n, sh)];
+  }
+}
+
+int small_path_max_n() { return 112; }
+
+int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0,
+                         int nb, const double2* S, double2* out, int* status, cudaStream_t st) {
+  size_t smem = (size_t)(c.n * c.n + c.n) * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    NED_CUDA(cudaFuncSetAttribute(gj_small_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  gj_small_fp64_kernel<<<nb, 512, smem, st>>>(c, m, eps, ebar, q0, S, out, status);
+  NED_LAUNCH_CHECK("gj_small_fp64_kernel");
+  return NEDMFT_OK;
+}
+
+// ------------------------------------------------------------------ blocked Gauss-Jordan, CUDA cores
+
+// Step k of blocked Gauss-Jordan on A (np x np, batch stride np*np):
+//   P = inv(A_KK)                                        gj_pivot_kernel
+//   R = P A_{K,:} with R_{:,K} = P;  C = A_{:,K} with C_K = -I   gj_panels_kernel
+//   A <- A(with rows K and columns K zeroed) - C R       gj_update_kernel
+template <class T, int NB>
+__global__ void __launch_bounds__(256) gj_pivot_kernel(cplx_t<T>* __restrict__ A, int np, int k0,
+                                                       cplx_t<T>* __restrict__ Pbuf, int* status) {
+  using C = cplx_t<T>;
+  __shared__ C p[NB * (NB + 1)];
+  __shared__ C col[NB];
+  const int b = blockIdx.x;
+  const C* a = A + (size_t)b * np * np;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, cc = e % NB;
+    p[r * (NB + 1) + cc] = a[(size_t)(k0 + r) * np + k0 + cc];
+  }
+  __syncthreads();
+  smem_gauss_jordan<T>(p, NB, NB + 1, col, sizeof(T) == 8 ? T(1e-12) : T(1e-6), status);
+  C* out = Pbuf + (size_t)b * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = p[(e / NB) * (NB + 1) + e % NB];
+}
+
+template <class T, int NB>
+__global__ void __launch_bounds__(256) gj_panels_kernel(const cplx_t<T>* __restrict__ A, int np, int k0,
+                                                        const cplx_t<T>* __restrict__ Pbuf,
+                                                        cplx_t<T>* __restrict__ Rbuf, cplx_t<T>* __restrict__ Cbuf) {
+  using C = cplx_t<T>;
+  constexpr int W = 32;
+  __shared__ C ps[NB][NB + 1];
+  __shared__ C as[NB][W + 1];
+  const int b = blockIdx.y;
+  const int j0 = blockIdx.x * W;
+  const C* a = A + (size_t)b * np * np;
+  const C* P = Pbuf + (size_t)b * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) ps[e / NB][e % NB] = P[e];
+  for (int e = threadIdx.x; e < NB * W; e += blockDim.x) {
+    int r = e / W, cc = e % W;
+    as[r][cc] = a[(size_t)(k0 + r) * np + j0 + cc];
+  }
+  __syncthreads();
+  C* R = Rbuf + (size_t)b * NB * np;
+  for (int e = threadIdx.x; e < NB * W; e += blockDim.x) {
+    int r = e / W, cc = e % W;
+    int j = j0 + cc;
+    C acc;
+    if (j >= k0 && j < k0 + NB) {
+      acc = ps[r][j - k0];
+    } else {
+      acc = mk<T>(0, 0);
+      for (int kk = 0; kk < NB; ++kk) cfma(acc, ps[r][kk], as[kk][cc]);
+    }
+    R[(size_t)r * np + j] = acc;
+  }
+  // C rows j0 .. j0+W-1
+  C* Cb = Cbuf + (size_t)b * np * NB;
+  for (int e = threadIdx.x; e < W * NB; e += blockDim.x) {
+    int i = j0 + e / NB, kk = e % NB;
+    C v;
+    if (i >= k0 && i < k0 + NB) v = mk<T>(i - k0 == kk ? T(-1) : T(0), 0);
+    else v = a[(size_t)i * np + k0 + kk];
+    Cb[(size_t)i * NB + kk] = v;
+  }
+}
+
+// 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs.
+template <class T, int NB>
+__global__ void __launch_bounds__(256) gj_update_kernel(cplx_t<T>* __restrict__ A, int np, int k0,
+                                                        const cplx_t<T>* __restrict__ Rbuf,
+                                                        const cplx_t<T>* __restrict__ Cbuf) {
+  using C = cplx_t<T>;
+  constexpr int TM = 64, TN = 64;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C (*cs)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smraw);
+  C (*rs)[TN] = reinterpret_cast<C (*)[TN]>(smraw + sizeof(C) * TM * (NB + 1));
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  const C* Cb = Cbuf + (size_t)b * np * NB;
+  const C* R = Rbuf + (size_t)b * NB * np;
+  for (int e = threadIdx.x; e < TM * NB; e += blockDim.x) cs[e / NB][e % NB] = Cb[(size_t)(i0 + e / NB) * NB + e % NB];
+  for (int e = threadIdx.x; e < NB * TN; e += blockDim.x) rs[e / TN][e % TN] = R[(size_t)(e / TN) * np + j0 + e % TN];
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = mk<T>(0, 0);
+#pragma unroll 4
+  for (int kk = 0; kk < NB; ++kk) {
+    C av[4], bv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) av[r] = cs[ty + 16 * r][kk];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bv[q] = rs[kk][tx + 16 * q];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cfma(acc[r][q], av[r], bv[q]);
+  }
+  C* a = A + (size_t)b * np * np;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int i = i0 + ty + 16 * r;
+    bool ik = (i >= k0 && i < k0 + NB);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int j = j0 + tx + 16 * q;
+      bool jk = (j >= k0 && j < k0 + NB);
+      C old = (ik || jk) ? mk<T>(0, 0) : a[(size_t)i * np + j];
+      a[(size_t)i * np + j] = csub(old, acc[r][q]);
+    }
+  }
+}
+
+template <class T>
+int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, cplx_t<T>* Rbuf, cplx_t<T>* Cbuf,
+                    int* status, cudaStream_t st) {
+  constexpr int NB = 32;
+  if (np % 64 != 0) return set_error(NEDMFT_EINVAL, "gj_blocked_simt: np=%d not a multiple of 64", np);
+  const size_t smem = sizeof(cplx_t<T>) * (64 * (NB + 1) + NB * 64);
+  NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int k0 = 0; k0 < np; k0 += NB) {
+    gj_pivot_kernel<T, NB><<<nb_batch, 256, 0, st>>>(A, np, k0, Pbuf, status);
+    NED_LAUNCH_CHECK("gj_pivot_kernel");
+    gj_panels_kernel<T, NB><<<dim3(np / 32, nb_batch), 256, 0, st>>>(A, np, k0, Pbuf, Rbuf, Cbuf);
+    NED_LAUNCH_CHECK("gj_panels_kernel");
+    const int slot = instr_begin(st);
+    gj_update_kernel<T, NB><<<dim3(np / 64, np / 64, nb_batch), 256, smem, st>>>(A, np, k0, Rbuf, Cbuf);
+    NED_LAUNCH_CHECK("gj_update_kernel");
+    const int live = n - k0 < NB ? (n - k0 > 0 ? n - k0 : 0) : NB;
+    instr_end(slot, st, 8.0 * (double)n * n * live * nb_batch);
+  }
+  return NEDMFT_OK;
+}
+template int gj_blocked_simt<double>(double2*, int, int, int, double2*, double2*, double2*, int*, cudaStream_t);
+template int gj_blocked_simt<float>(float2*, int, int, int, float2*, float2*, float2*, int*, cudaStream_t);
+
+// ------------------------------------------------------------------ batched complex GEMM, CUDA cores
+
+// Cout[b] = A[b] (m x k) * B[b] (k x n), all row-major with the given leading
+// dimensions and batch strides (stride 0 shares an operand).  m, n multiples
+// of 64, k a multiple of 32.
+template <class T>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(const cplx_t<T>* __restrict__ A, int lda, size_t sa,
+                                                        const cplx_t<T>* __restrict__ B, int ldb, size_t sb,
+                                                        cplx_t<T>* __restrict__ Cout, int ldc, size_t sc, int k) {
+  using C = cplx_t<T>;
+  constexpr int TM = 64, TN = 64, TK = 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C (*as_)[TK + 1] = reinterpret_cast<C (*)[TK + 1]>(smraw);
+  C (*bs_)[TN] = reinterpret_cast<C (*)[TN]>(smraw + sizeof(C) * TM * (TK + 1));
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  const C* a = A + b * sa;
+  const C* bm = B + b * sb;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = mk<T>(0, 0);
+  for (int kb = 0; kb < k; kb += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) as_[e / TK][e % TK] = a[(size_t)(i0 + e / TK) * lda + kb + e % TK];
+    for (int e = threadIdx.x; e < TK * TN; e += blockDim.x) bs_[e / TN][e % TN] = bm[(size_t)(kb + e / TN) * ldb + j0 + e % TN];
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      C av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = as_[ty + 16 * r][kk];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = bs_[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[r][q], av[r], bv[q]);
+    }
+    __syncthreads();
+  }
+  C* cm = Cout + b * sc;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cm[(size_t)(i0 + ty + 16 * r) * ldc + j0 + tx + 16 * q] = acc[r][q];
+}
+
+template <class T>
+int gemm_simt(const cplx_t<T>* A, int lda, size_t sa, const cplx_t<T>* B, int ldb, size_t sb, cplx_t<T>* Cout,
+              int ldc, size_t sc, int m, int n, int k, int batch, cudaStream_t st) {
+  if (m % 64 || n % 64 || k % 32) return set_error(NEDMFT_EINVAL, "gemm_simt: bad shape %d x %d x %d", m, n, k);
+  const size_t smem = sizeof(cplx_t<T>) * (64 * 33 + 32 * 64);
+  NED_CUDA(cudaFuncSetAttribute(gemm_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  gemm_simt_kernel<T><<<dim3(n / 64, m / 64, batch), 256, smem, st>>>(A, lda, sa, B, ldb, sb, Cout, ldc, sc, k);
+  NED_LAUNCH_CHECK("gemm_simt_kernel");
+  return NEDMFT_OK;
+}
+template int gemm_simt<float>(const float2*, int, size_t, const float2*, int, size_t, float2*, int, size_t, int, int,
+                              int, int, cudaStream_t);
+template int gemm_simt<double>(const double2*, int, size_t, const double2*, int, size_t, double2*, int, size_t, int,
+                               int, int, int, cudaStream_t);
+
+// ------------------------------------------------------------------ refinement residual
+
+// R'[b] = I - A'_q X'[b] with A'_q = P (B_q - S):
+//   R'[r][j] = delta_rj - (B_q X')[i][j] + T[b][i][j],  i = row of A_q behind row r,
+// where T = S X' (computed by a GEMM, any precision) and (B_q X')[i][j] uses
+// the bidiagonal entries of B_q in FP64.  Rows/columns >= N: R' = I - X'.
+template <class T>
+__global__ void residual_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                const double* __restrict__ ebar_d, int q0, const cplx_t<T>* __restrict__ X,
+                                const cplx_t<T>* __restrict__ Tm, int ldt, size_t st_, cplx_t<T>* __restrict__ R,
+                                int np) {
+  const int b = blockIdx.y;
+  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+  const bool sh = shifted_point(m, eps);
+  const cplx_t<T>* x = X + (size_t)b * np * np;
+  const cplx_t<T>* t = Tm + b * st_;
+  cplx_t<T>* out = R + (size_t)b * np * np;
+  const size_t total = (size_t)np * np;
+  const double2 bdiag = make_double2(0.0, 1.0);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(e / np), j = (int)(e % np);
+    double2 v = make_double2(r == j ? 1.0 : 0.0, 0.0);
+    if (r < c.n) {
+      int i = sh ? (r + 1 == c.n ? 0 : r + 1) : r;
+      double2 bx = cmul(bdiag, to_d(x[(size_t)i * np + j]));
+      if (i >= 1) bx = cadd(bx, cmul(b_sub(c, m, eps, ebar, i), to_d(x[(size_t)(i - 1) * np + j])));
+      if (i == 0) bx = cadd(bx, cmul(b_corner(c, m, eps), to_d(x[(size_t)(c.n - 1) * np + j])));
+      v = csub(v, bx);
+      v = cadd(v, to_d(t[(size_t)i * ldt + j]));
+    } else {
+      v = csub(v, to_d(x[(size_t)r * np + j]));
+    }
+    out[e] = cvt<T>(v);
+  }
+}
+
+template <class T>
+int launch_residual(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0, int nb,
+                    const cplx_t<T>* X, const cplx_t<T>* Tm, int ldt, size_t st_, cplx_t<T>* R, int np,
+                    cudaStream_t st) {
+  size_t total = (size_t)np * np;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 2048) bx = 2048;
+  residual_kernel<T><<<dim3(bx, nb), 256, 0, st>>>(c, m, eps, ebar, q0, X, Tm, ldt, st_, R, np);
+  NED_LAUNCH_CHECK("residual_kernel");
+  return NEDMFT_OK;
+}
+template int launch_residual<float>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
+                                    const float2*, const float2*, int, size_t, float2*, int, cudaStream_t);
+
+// ------------------------------------------------------------------ FP64 reductions over the points
+
+// gloc[i][j] (= or +=) sum_b wq[q0+b] (X[b] + dX[b])[i][col(j)], b ascending,
+// col = unshift_col if `cycled` (the batch holds X' = (P A)^-1).
+template <class T>
+__global__ void reduce_gloc_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                   const double* __restrict__ wq_d, int q0, int nb, const cplx_t<T>* __restrict__ X,
+                                   const cplx_t<T>* __restrict__ dX, int ldx, bool cycled, bool first,
+                                   double2* __restrict__ gloc) {
+  const size_t total = (size_t)c.n * c.n;
+  const size_t bstride = (size_t)ldx * ldx;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / c.n), j = (int)(e % c.n);
+    double2 acc = first ? make_double2(0.0, 0.0) : gloc[e];
+    for (int b = 0; b < nb; ++b) {
+      const int q = q0 + b;
+      const bool sh = cycled && shifted_point(m, eps_d[q]);
+      const size_t off = (size_t)b * bstride + (size_t)i * ldx + unshift_col(j, c.n, sh);
+      double2 v = to_d(X[off]);
+      if (dX) v = cadd(v, to_d(dX[off]));
+      const double w = wq_d[q];
+      acc.x = fma(w, v.x, acc.x);
+      acc.y = fma(w, v.y, acc.y);
+    }
+    gloc[e] = acc;
+  }
+}
+
+// jacc[m] (= or +=) sum_b wq ebar_q(t_m) G_q[m][2 N_t - m].
+template <class T>
+__global__ void reduce_current_kernel(ContourDev c, ModelDev mo, const double* __restrict__ eps_d,
+                                      const double* __restrict__ ebar_d, const double* __restrict__ wq_d, int q0,
+                                      int nb, const cplx_t<T>* __restrict__ X, const cplx_t<T>* __restrict__ dX,
+                                      int ldx, bool cycled, bool first, double2* __restrict__ jacc) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mm >= c.nt) return;
+  const double t = t_re(c, mm);
+  const int jcol = 2 * c.nt - mm;
+  double2 acc = first ? make_double2(0.0, 0.0) : jacc[mm];
+  for (int b = 0; b < nb; ++b) {
+    const int q = q0 + b;
+    const double eps = eps_d[q];
+    const bool sh = cycled && shifted_point(mo, eps);
+    const size_t off = (size_t)b * ldx * ldx + (size_t)mm * ldx + unshift_col(jcol, c.n, sh);
+    double2 v = to_d(X[off]);
+    if (dX) v = cadd(v, to_d(dX[off]));
+    const double w = wq_d[q] * ebar_at(t, eps, ebar_d[q], mo.E);
+    acc.x = fma(w, v.x, acc.x);
+    acc.y = fma(w, v.y, acc.y);
+  }
+  jacc[mm] = acc;
+}
+
+// j = Re(i acc) = -acc.y, j_imag = Im(i acc) = acc.x.
+__global__ void finish_current_kernel(int nt, const double2* __restrict__ jacc, double* __restrict__ j,
+                                      double* __restrict__ ji) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mm >= nt) return;
+  if (j) j[mm] = -jacc[mm].y;
+  if (ji) ji[mm] = jacc[mm].x;
+}
+
+template <class T>
+int launch_reduce(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, const double* wq,
+                  int q0, int nb, const cplx_t<T>* X, const cplx_t<T>* dX, int ldx, bool cycled, bool first,
+                  double2* gloc, double2* jacc, cudaStream_t st) {
+  size_t total = (size_t)c.n * c.n;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 152 * 8) bx = 152 * 8;
+  reduce_gloc_kernel<T><<<bx, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dX, ldx, cycled, first, gloc);
+  NED_LAUNCH_CHECK("reduce_gloc_kernel");
+  if (jacc) {
+    reduce_current_kernel<T><<<ceil_div(c.nt, 128), 128, 0, st>>>(c, m, eps, ebar, wq, q0, nb, X, dX, ldx, cycled,
+                                                                  first, jacc);
+    NED_LAUNCH_CHECK("reduce_current_kernel");
+  }
+  return NEDMFT_OK;
+}
+template int launch_reduce<double>(const ContourDev&, const ModelDev&, const double*, const double*, const double*,
+                                   int, int, const double2*, const double2*, int, bool, bool, double2*, double2*,
+                                   cudaStream_t);
+template int launch_reduce<float>(const ContourDev&, const ModelDev&, const double*, const double*, const double*,
+                                  int, int, const float2*, const float2*, int, bool, bool, double2*, double2*,
+                                  cudaStream_t);
+
+int launch_finish_current(int nt, const double2* jacc, double* j, double* ji, cudaStream_t st) {
+  finish_current_kernel<<<ceil_div(nt, 128), 128, 0, st>>>(nt, jacc, j, ji);
+  NED_LAUNCH_CHECK("finish_current_kernel");
+  return NEDMFT_OK;
+}
+
+// ------------------------------------------------------------------ conversions
+
+__global__ void to_f32_kernel(const double2* __restrict__ in, int n, int ldi, float2* __restrict__ out, int ldo,
+                              int rows_out, int cols_out) {
+  const size_t total = (size_t)rows_out * cols_out;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / cols_out), j = (int)(e % cols_out);
+    double2 v = (i < n && j < n) ? in[(size_t)i * ldi + j] : make_double2(0.0, 0.0);
+    out[(size_t)i * ldo + j] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+int launch_to_f32_padded(const double2* in, int n, float2* out, int np, cudaStream_t st) {
+  size_t total = (size_t)np * np;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 4096) bx = 4096;
+  to_f32_kernel<<<bx, 256, 0, st>>>(in, n, n, out, np, np, np);
+  NED_LAUNCH_CHECK("to_f32_kernel");
+  return NEDMFT_OK;
+}
+
+}  // namespace nedmft

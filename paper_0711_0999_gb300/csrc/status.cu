@@ -1,0 +1,149 @@
+// Status codes, the per-thread error message and the device status word.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nedmft {
+
+namespace {
+thread_local std::string g_last_error;
+
+// One status word per device (a file-scope device variable exists once on
+// every device that loads the library).
+__device__ int g_status_word;
+
+constexpr int kMaxDevices = 64;
+int* g_status_addr[kMaxDevices] = {nullptr};
+std::mutex g_status_mu;
+}  // namespace
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_error(NEDMFT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+namespace {
+std::atomic<bool> g_instr_on{false};
+std::atomic<bool> g_instr_timing{false};
+std::atomic<long long> g_launches{0};
+std::mutex g_instr_mu;
+struct Slot { cudaEvent_t a, b; double flops; };
+std::vector<Slot> g_slots;
+size_t g_slot_used = 0;
+}  // namespace
+
+void instr_count() {
+  if (g_instr_on.load(std::memory_order_relaxed)) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+bool instr_timing() { return g_instr_timing.load(std::memory_order_relaxed); }
+int instr_begin(cudaStream_t st) {
+  if (!instr_timing()) return -1;
+  std::lock_guard<std::mutex> lk(g_instr_mu);
+  if (g_slot_used == g_slots.size()) {
+    Slot s{};
+    if (cudaEventCreate(&s.a) != cudaSuccess || cudaEventCreate(&s.b) != cudaSuccess) return -1;
+    g_slots.push_back(s);
+  }
+  int k = (int)g_slot_used++;
+  g_slots[k].flops = 0.0;
+  if (cudaEventRecord(g_slots[k].a, st) != cudaSuccess) return -1;
+  return k;
+}
+void instr_end(int slot, cudaStream_t st, double flops) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_instr_mu);
+  cudaEventRecord(g_slots[slot].b, st);
+  g_slots[slot].flops = flops;
+}
+
+int* device_status_ptr() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  if (!g_status_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+    g_status_addr[dev] = static_cast<int*>(p);
+  }
+  return g_status_addr[dev];
+}
+
+}  // namespace nedmft
+
+using namespace nedmft;
+
+extern "C" const char* nedmft_status_string(int status) {
+  switch (status) {
+    case NEDMFT_OK: return "ok";
+    case NEDMFT_EINVAL: return "invalid argument";
+    case NEDMFT_ENOMEM: return "workspace too small";
+    case NEDMFT_ECUDA: return "CUDA runtime error";
+    case NEDMFT_ESINGULAR: return "pivot below threshold (matrix singular to working precision)";
+    case NEDMFT_ETIMEOUT: return "bounded device wait expired";
+    case NEDMFT_ENOTCONV: return "not converged within max_iter";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* nedmft_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* nedmft_version(void) { return "nedmft-gb300 0.1 (sm_103a)"; }
+
+extern "C" int nedmft_check_status(void* stream) {
+  int* p = device_status_ptr();
+  if (!p) return set_error(NEDMFT_ECUDA, "cannot locate the device status word");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int host = 0;
+  NED_CUDA(cudaMemcpyAsync(&host, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NED_CUDA(cudaStreamSynchronize(s));
+  if (host != DS_OK) {
+    NED_CUDA(cudaMemsetAsync(p, 0, sizeof(int), s));
+    NED_CUDA(cudaStreamSynchronize(s));
+  }
+  if (host == DS_SINGULAR) return set_error(NEDMFT_ESINGULAR, "a Gauss-Jordan pivot fell below the threshold");
+  if (host == DS_TIMEOUT) return set_error(NEDMFT_ETIMEOUT, "a bounded device wait expired");
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_instrument(int enable, int timing) {
+  std::lock_guard<std::mutex> lk(g_instr_mu);
+  g_instr_on = enable != 0;
+  g_instr_timing = enable != 0 && timing != 0;
+  g_launches = 0;
+  g_slot_used = 0;
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches, double* timed_ms,
+                                      double* timed_flops) {
+  std::lock_guard<std::mutex> lk(g_instr_mu);
+  double ms = 0.0, fl = 0.0;
+  for (size_t k = 0; k < g_slot_used; ++k) {
+    NED_CUDA(cudaEventSynchronize(g_slots[k].b));
+    float t = 0.0f;
+    NED_CUDA(cudaEventElapsedTime(&t, g_slots[k].a, g_slots[k].b));
+    ms += t;
+    fl += g_slots[k].flops;
+  }
+  if (launches) *launches = g_launches.load();
+  if (timed_launches) *timed_launches = (int64_t)g_slot_used;
+  if (timed_ms) *timed_ms = ms;
+  if (timed_flops) *timed_flops = fl;
+  return NEDMFT_OK;
+}
