@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = 2 x cores)")
+    ap.add_argument("--n-quad", type=int, default=0, help="override the quadrature size (profiling runs only)")
     return ap.parse_args()
 
 
@@ -234,7 +235,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.n_quad:
+        W["n_quad"] = args.n_quad
+        W["name"] += f" [profiling subset: {args.n_quad}x{args.n_quad} points]"
     grid = api.contour_grid(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"])
     # independent run per rank (weak scaling): rank r solves U + 0.05 r
     U = W["U"] + 0.05 * rank

@@ -31,7 +31,7 @@ Path choose_path(const nedmft_contour& c, nedmft_precision p) {
 
 int default_batch(const nedmft_contour& c, int nq, Path path) {
   const size_t np = padded(c.n_c);
-  size_t per = 0, budget = (size_t)8 << 30;  // about 8 GB of batch buffers
+  size_t per = 0, budget = (size_t)16 << 30;  // about 16 GB of batch buffers
   int cap = 152;
   switch (path) {
     case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
@@ -79,8 +79,8 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
       L.extra = align256(sizeof(float2) * np * np);  // S in FP32, padded
       break;
     case Path::MixedUmma:
-      L.batch = align256(umma_batch_bytes_per_matrix((int)np) * mb);
-      L.extra = align256(umma_shared_bytes((int)np));
+      L.batch = align256(umma_batch_bytes((int)np, (int)mb));
+      L.extra = align256(umma_shared_bytes((int)np, nq));
       break;
   }
   L.total = L.S + L.gscratch + L.jacc + L.batch + L.pbuf + L.rbuf + L.cbuf + L.extra + 256;
@@ -117,7 +117,7 @@ int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* s
     if ((rc = launch_to_f32_padded(S, cd.n, reinterpret_cast<float2*>(extra), np, st))) return rc;
   }
   if (L.path == Path::MixedUmma) {
-    if ((rc = umma_prepare_shared(cd, S, np, extra, st))) return rc;
+    if ((rc = umma_prepare_shared(cd, S, np, eps, ebar, wq, nq, extra, st))) return rc;
   }
   for (int q0 = 0; q0 < nq; q0 += mb) {
     const int nb = (nq - q0) < mb ? (nq - q0) : mb;

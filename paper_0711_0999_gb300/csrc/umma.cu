@@ -1,14 +1,1047 @@
+// Tensor-core (tcgen05) path of the lattice step.
+//
+// Gauss-Jordan on A'_q (np x np, FP32 complex, batch of nb matrices) in
+// steps of 128 columns.  Step k0:
+//   gj_pivot_pack   P = inv(A_KK) in shared memory (FP32), packed bf16 hi/lo
+//   gj_panel_pack   C' = A_{:,K} (C'_K = -I) packed as the update's A operand;
+//                   A_{K,:}^T (A_KK -> I), 2x2 real-embedded, packed as the
+//                   R-product's B operand
+//   umma_gemm       R = P A_{K,:} (bf16x3), written packed as the update's B
+//   umma_gemm       A <- A (rows K, cols K zeroed) - C' R (bf16x3)
+// A complex product is a real GEMM on interleaved storage: the A operand is
+// the interleaved row (re, im, re, im, ...), the B operand the 2x2 real
+// embedding [[re, -im], [im, re]] of each complex entry, so the output lands
+// interleaved.
+#include "lattice.cuh"
 #include "umma.cuh"
+#include "umma_core.cuh"
 
 namespace nedmft {
 
-size_t umma_batch_bytes_per_matrix(int np) { return sizeof(float2) * (size_t)np * np; }
-int umma_default_batch(int) { return 1; }
-size_t umma_shared_bytes(int) { return 0; }
-int umma_prepare_shared(const ContourDev&, const double2*, int, char*, cudaStream_t) { return NEDMFT_OK; }
-int umma_lattice_batch(const ContourDev&, const ModelDev&, const double*, const double*, const double*, int, int, int,
-                       const double2*, char*, char*, bool, double2*, double2*, int*, cudaStream_t) {
-  return set_error(NEDMFT_EINVAL, "lattice: the NEDMFT_MIXED_BF16 tensor-core path is not built in this library");
+using namespace umma;
+
+namespace {
+
+constexpr int kNb = 128;        // Gauss-Jordan block (complex columns)
+constexpr int kKt = 2 * kNb / kTileK;  // K tiles of the rank-kNb products (4)
+
+// ------------------------------------------------------------------ the GEMM kernel
+
+// One 128 x BN output tile per CTA: C = sum over pairs of A_slice(a) B_slice(b)^T,
+// K = kt * 64, accumulated in FP32 in TMEM.  Warp 0: TMA producer; warp 1:
+// TMEM allocator and MMA issuer; warps 2-5: epilogue (one TMEM lane each).
+struct GemmParams {
+  const __nv_bfloat16* a;
+  size_t a_batch;        // elements between batch entries (0: shared operand)
+  size_t a_slice;        // elements between slices
+  const __nv_bfloat16* b;
+  size_t b_batch;
+  size_t b_slice;
+  int kt;                // K tiles
+  int* status;
+};
+
+template <int BN, int SA, int SB, int STAGES>
+struct Cfg {
+  static constexpr int kBn = BN;
+  static constexpr int kSa = SA;
+  static constexpr int kSb = SB;
+  static constexpr int kStages = STAGES;
+  static constexpr int kBTiles = BN / kTileRows;
+  static constexpr int kStageBytes = (SA + SB * kBTiles) * kTileBytes;
+  static constexpr int kSmem = STAGES * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+};
+
+// bf16x3: hi*hi + hi*lo + lo*hi, one accumulator.
+struct Split3 {
+  static constexpr int kPairs = 3;
+  __device__ static int a(int p) { return p == 2 ? 1 : 0; }
+  __device__ static int b(int p) { return p == 1 ? 1 : 0; }
+};
+
+template <class C, class Pairs, class Epi>
+__device__ __forceinline__ void umma_gemm_body(const GemmParams& p, const Epi& epi) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* acc_full = empty + C::kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y, bidx = blockIdx.z;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, C::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const __nv_bfloat16* a = p.a + bidx * p.a_batch;
+      const __nv_bfloat16* b = p.b + bidx * p.b_batch;
+      int issued = 0;
+      for (int kt = 0; kt < p.kt; ++kt) {
+        const int s = kt % C::kStages;
+        const uint32_t ph = (kt / C::kStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) break;
+        unsigned char* st = smem + s * C::kStageBytes;
+        mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+        for (int sa = 0; sa < C::kSa; ++sa)
+          bulk_g2s(st + sa * kTileBytes, a + sa * p.a_slice + ((size_t)mt * p.kt + kt) * kTileElems, kTileBytes,
+                   &full[s]);
+        for (int sb = 0; sb < C::kSb; ++sb)
+          for (int u = 0; u < C::kBTiles; ++u)
+            bulk_g2s(st + (C::kSa + sb * C::kBTiles + u) * kTileBytes,
+                     b + sb * p.b_slice + ((size_t)(nt * C::kBTiles + u) * p.kt + kt) * kTileElems, kTileBytes,
+                     &full[s]);
+        issued = kt + 1;
+      }
+      // never leave a copy in flight: wait (bounded) for every stage issued in the last round
+      for (int kt = issued - C::kStages < 0 ? 0 : issued - C::kStages; kt < issued; ++kt) {
+        const int s = kt % C::kStages;
+        const uint32_t ph = (kt / C::kStages) & 1;
+        uint64_t t0 = global_ns();
+        while (!mbar_test(&full[s], ph) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
+      for (int kt = 0; kt < p.kt; ++kt) {
+        const int s = kt % C::kStages;
+        const uint32_t ph = (kt / C::kStages) & 1;
+        if (!mbar_wait(&full[s], ph, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kTileK / 16; ++kk) {
+#pragma unroll
+          for (int q = 0; q < Pairs::kPairs; ++q) {
+            const uint32_t a_addr = st + Pairs::a(q) * kTileBytes + kk * 256;
+            const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * C::kBTiles) * kTileBytes + kk * 256;
+            mma_bf16(tmem, smem_desc(a_addr, 128, 1024), smem_desc(b_addr, 128, 1024), idesc,
+                     (kt > 0 || kk > 0 || q > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(acc_full);
+    }
+  } else {
+    // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    if (mbar_wait(acc_full, 0, abort_flag)) {
+      tc_fence_after();
+      if (!*abort_flag) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < C::kBn; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+          epi(bidx, mt, nt, row, c0, v);
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    // the tensor core must be idle before the columns are released
+    uint64_t t0 = global_ns();
+    while (!mbar_test(acc_full, 0) && global_ns() - t0 < kWaitNs) {
+    }
+    tc_fence_after();
+    tmem_dealloc(tmem, C::kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && p.status) atomicCAS(p.status, 0, DS_TIMEOUT);
+}
+
+template <class C, class Pairs, class Epi>
+__global__ void __launch_bounds__(192, 1) umma_gemm_kernel(GemmParams p, Epi epi) {
+  umma_gemm_body<C, Pairs, Epi>(p, epi);
+}
+
+// the same GEMM, skipping the matrices whose flag is 0
+template <class C, class Pairs, class Epi>
+__global__ void __launch_bounds__(192, 1) umma_gemm_flag_kernel(GemmParams p, Epi epi, const int* flags, int q0) {
+  if (!flags[q0 + blockIdx.z]) return;
+  umma_gemm_body<C, Pairs, Epi>(p, epi);
+}
+
+template <class C, class Pairs, class Epi>
+int launch_gemm(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    NED_CUDA(cudaFuncSetAttribute(umma_gemm_kernel<C, Pairs, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  C::kSmem));
+    attr = true;
+  }
+  dim3 grid(n_tiles, m_tiles, batch);
+  umma_gemm_kernel<C, Pairs, Epi><<<grid, 192, C::kSmem, st>>>(p, epi);
+  NED_LAUNCH_CHECK("umma_gemm_kernel");
+  return NEDMFT_OK;
+}
+
+using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (192 KB)
+
+// ------------------------------------------------------------------ epilogues
+
+// A <- A(rows K and columns K zeroed) - acc, A interleaved FP32 (row stride 2 np floats).
+struct EpiUpdate {
+  float* A;
+  size_t bstride;  // floats between matrices
+  int np, k0;
+  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+    const int i = mt * kTileRows + r;
+    const int n0 = nt * CfgGJ::kBn + c0;  // real column
+    float* row = A + b * bstride + (size_t)i * 2 * np + n0;
+    const bool ik = (i >= k0 && i < k0 + kNb);
+    const int j0 = n0 >> 1;  // first complex column of the chunk
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float4 o = ik ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
+      const int ja = j0 + 2 * u;
+      if (ja >= k0 && ja < k0 + kNb) { o.x = 0.f; o.y = 0.f; }
+      if (ja + 1 >= k0 && ja + 1 < k0 + kNb) { o.z = 0.f; o.w = 0.f; }
+      o.x -= v[4 * u]; o.y -= v[4 * u + 1]; o.z -= v[4 * u + 2]; o.w -= v[4 * u + 3];
+      *reinterpret_cast<float4*>(row + 4 * u) = o;
+    }
+  }
+};
+
+// R (kNb x np complex, acc rows = R rows) -> the update's B operand image:
+// rows n = 2j, 2j+1; k = 2r, 2r+1 with [[re, -im], [im, re]].
+struct EpiRPack {
+  __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 kNb)
+  size_t bstride;       // elements between matrices
+  size_t slice;         // elements between slices
+  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+    __nv_bfloat16* base = img + b * bstride;
+    const int n0 = nt * CfgGJ::kBn + c0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int j = (n0 >> 1) + u;
+      const float re = v[2 * u], im = v[2 * u + 1];
+      __nv_bfloat16 rh, rl, ih, il, nh, nl;
+      split2(re, rh, rl);
+      split2(im, ih, il);
+      split2(-im, nh, nl);
+      const size_t o0 = img_offset(2 * j, 2 * r, kKt);      // (re, -im)
+      const size_t o1 = img_offset(2 * j + 1, 2 * r, kKt);  // (im, re)
+      *reinterpret_cast<__nv_bfloat162*>(base + o0) = __halves2bfloat162(rh, nh);
+      *reinterpret_cast<__nv_bfloat162*>(base + o1) = __halves2bfloat162(ih, rh);
+      *reinterpret_cast<__nv_bfloat162*>(base + slice + o0) = __halves2bfloat162(rl, nl);
+      *reinterpret_cast<__nv_bfloat162*>(base + slice + o1) = __halves2bfloat162(il, rl);
+    }
+  }
+};
+
+// ------------------------------------------------------------------ panel kernels (CUDA cores)
+
+// P = inv(A_KK) (kNb x kNb, FP32, no pivoting -- the static row order makes
+// the pivots safe) written as the R-product's A operand: row r, k = 2c / 2c+1.
+__global__ void __launch_bounds__(512) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
+                                                            __nv_bfloat16* __restrict__ pimg, size_t pstride,
+                                                            size_t pslice, int* status) {
+  extern __shared__ float2 sp[];
+  constexpr int ld = kNb + 1;
+  float2* a = sp;
+  float2* col = sp + kNb * ld;
+  const int b = blockIdx.x;
+  const float2* src = A + (size_t)b * np * np;
+  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+    const int r = e / kNb, c = e % kNb;
+    a[r * ld + c] = src[(size_t)(k0 + r) * np + k0 + c];
+  }
+  __syncthreads();
+  for (int k = 0; k < kNb; ++k) {
+    if (threadIdx.x < kNb) col[threadIdx.x] = a[threadIdx.x * ld + k];
+    __syncthreads();
+    float2 pinv;
+    const bool ok = cinv_guard<float>(col[k], pinv, 1e-6f);
+    if (!ok && threadIdx.x == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
+    if (threadIdx.x < kNb) {
+      const int t = threadIdx.x;
+      a[k * ld + t] = (t == k) ? pinv : cmul(a[k * ld + t], pinv);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+      const int i = e / kNb, j = e % kNb;
+      if (i == k) continue;
+      const float2 f = col[i];
+      if (j == k) {
+        const float2 w = cmul(f, pinv);
+        a[i * ld + k] = make_float2(-w.x, -w.y);
+      } else {
+        const float2 rk = a[k * ld + j];
+        float2 w = a[i * ld + j];
+        w.x -= f.x * rk.x - f.y * rk.y;
+        w.y -= f.x * rk.y + f.y * rk.x;
+        a[i * ld + j] = w;
+      }
+    }
+    __syncthreads();
+  }
+  __nv_bfloat16* dst = pimg + b * pstride;
+  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+    const int r = e / kNb, c = e % kNb;
+    const float2 z = a[r * ld + c];
+    __nv_bfloat16 rh, rl, ih, il;
+    split2(z.x, rh, rl);
+    split2(z.y, ih, il);
+    const size_t o = img_offset(r, 2 * c, kKt);
+    *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
+    *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
+  }
+}
+
+// Block x of matrix y: rows x*128 .. +127 of C' (the update's A operand) and
+// columns x*128 .. +127 of the embedded A_{K,:}^T (the R-product's B operand).
+__global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __restrict__ A, int np, int k0,
+                                                            __nv_bfloat16* __restrict__ cimg, size_t cstride,
+                                                            size_t cslice, __nv_bfloat16* __restrict__ timg,
+                                                            size_t tstride, size_t tslice) {
+  const int b = blockIdx.y;
+  const int base = blockIdx.x * 128;
+  const float2* src = A + (size_t)b * np * np;
+  __nv_bfloat16* cd = cimg + b * cstride;
+  __nv_bfloat16* td = timg + b * tstride;
+  for (int e = threadIdx.x; e < 128 * kNb; e += blockDim.x) {
+    // C'[i][c], i = base + e / kNb, c = e % kNb (consecutive threads: consecutive c)
+    {
+      const int i = base + e / kNb, c = e % kNb;
+      float2 z;
+      if (i >= k0 && i < k0 + kNb) z = make_float2(i - k0 == c ? -1.f : 0.f, 0.f);
+      else z = src[(size_t)i * np + k0 + c];
+      __nv_bfloat16 rh, rl, ih, il;
+      split2(z.x, rh, rl);
+      split2(z.y, ih, il);
+      const size_t o = img_offset(i, 2 * c, kKt);
+      *reinterpret_cast<__nv_bfloat162*>(cd + o) = __halves2bfloat162(rh, ih);
+      *reinterpret_cast<__nv_bfloat162*>(cd + cslice + o) = __halves2bfloat162(rl, il);
+    }
+    // T[n][k]: column j = base + e % 128 of A_{K,:}, row c = e / 128
+    {
+      const int j = base + (e & 127), c = e >> 7;
+      float2 z;
+      if (j >= k0 && j < k0 + kNb) z = make_float2(j - k0 == c ? 1.f : 0.f, 0.f);
+      else z = src[(size_t)(k0 + c) * np + j];
+      __nv_bfloat16 rh, rl, ih, il, nh, nl;
+      split2(z.x, rh, rl);
+      split2(z.y, ih, il);
+      split2(-z.y, nh, nl);
+      const size_t o0 = img_offset(2 * j, 2 * c, kKt);
+      const size_t o1 = img_offset(2 * j + 1, 2 * c, kKt);
+      *reinterpret_cast<__nv_bfloat162*>(td + o0) = __halves2bfloat162(rh, nh);
+      *reinterpret_cast<__nv_bfloat162*>(td + o1) = __halves2bfloat162(ih, rh);
+      *reinterpret_cast<__nv_bfloat162*>(td + tslice + o0) = __halves2bfloat162(rl, nl);
+      *reinterpret_cast<__nv_bfloat162*>(td + tslice + o1) = __halves2bfloat162(il, rl);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ buffer layout per matrix
+
+struct GjBuffers {
+  size_t mat, pimg, cimg, timg, rimg, total;  // bytes, each 1024-aligned
+};
+
+size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+GjBuffers gj_buffers(int np) {
+  GjBuffers g{};
+  g.mat = align1k(sizeof(float2) * (size_t)np * np);
+  g.pimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)kNb * 2 * kNb);
+  g.cimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * kNb);
+  g.timg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * kNb);
+  g.rimg = g.timg;
+  g.total = g.mat + g.pimg + g.cimg + g.timg + g.rimg;
+  return g;
+}
+
+}  // namespace
+
+// Gauss-Jordan inversion of nb matrices (np x np FP32 complex, batch stride
+// np*np, np a multiple of 128) on the tensor cores.  `scratch` holds the
+// packed panels: gj_buffers(np) minus the matrix, times nb.
+int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st) {
+  if (np % kNb) return set_error(NEDMFT_EINVAL, "gj_blocked_umma: np=%d not a multiple of %d", np, kNb);
+  const GjBuffers g = gj_buffers(np);
+  const size_t per = g.pimg + g.cimg + g.timg + g.rimg;
+  __nv_bfloat16* pimg = reinterpret_cast<__nv_bfloat16*>(scratch);
+  __nv_bfloat16* cimg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg);
+  __nv_bfloat16* timg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg + g.cimg);
+  __nv_bfloat16* rimg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg + g.cimg + g.timg);
+  const size_t pstride = per / 2, pslice = (size_t)kNb * 2 * kNb;
+  const size_t cslice = (size_t)np * 2 * kNb;
+  const size_t tslice = (size_t)2 * np * 2 * kNb;
+  const size_t smem_piv = sizeof(float2) * (kNb * (kNb + 1) + kNb);
+  static bool attr = false;
+  if (!attr) {
+    NED_CUDA(cudaFuncSetAttribute(gj_pivot_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_piv));
+    attr = true;
+  }
+  for (int k0 = 0; k0 < np; k0 += kNb) {
+    gj_pivot_pack_kernel<<<nb, 512, smem_piv, st>>>(A, np, k0, pimg, pstride, pslice, status);
+    NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
+    gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, k0, cimg, pstride, cslice, timg, pstride, tslice);
+    NED_LAUNCH_CHECK("gj_panel_pack_kernel");
+    {  // R = P A_{K,:}, 128 x 2np, K = 256
+      GemmParams p{pimg, pstride, pslice, timg, pstride, tslice, kKt, status};
+      EpiRPack epi{rimg, pstride, tslice};
+      int rc = launch_gemm<CfgGJ, Split3>(p, 2 * np / CfgGJ::kBn, 1, nb, epi, st);
+      if (rc) return rc;
+    }
+    {  // A <- A - C' R, np x 2np, K = 256
+      GemmParams p{cimg, pstride, cslice, rimg, pstride, tslice, kKt, status};
+      EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0};
+      const int slot = instr_begin(st);
+      int rc = launch_gemm<CfgGJ, Split3>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
+      if (rc) return rc;
+      const int live = n - k0 < kNb ? (n - k0 > 0 ? n - k0 : 0) : kNb;
+      instr_end(slot, st, 8.0 * (double)n * n * live * nb);
+    }
+  }
+  return NEDMFT_OK;
+}
+
+// ------------------------------------------------------------------ refinement
+//
+// One refinement step X1' = X' + X' R' with R' = I - A' X'.  With S split
+// into its entries on the pattern of B_q (diagonal, subdiagonal, boundary
+// element) and the rest S_d,
+//   R'[r] = e_r - [(B - S_sp) X'][i] + [S_d X'][i],   i = row of A behind row r,
+// the sparse product is formed exactly (double-float) in the epilogue and the
+// dense product S_d X' by an Ozaki split on the bf16 tensor cores: each
+// operand is scaled (rows of S_d, columns of X') by a power of two and cut
+// into kOzS integer slices of kOzBits bits; every slice product is exact,
+// products of equal total slice order d share an FP32 accumulator, and the
+// K range is cut into chunks short enough for those integer sums to stay
+// exact; the chunk sums are added in double-float.  Only points outside the
+// smallest-weight tail (total weight <= kRefineTail) are refined.
+
+namespace {
+
+constexpr int kOzS = 4;           // slices per operand
+constexpr int kOzBits = 7;        // bits per slice
+constexpr int kOzPairs = 10;      // slice pairs with a + b <= kOzS - 1
+constexpr int kOzBn = 64;         // output columns per tile (32 complex)
+constexpr int kOzChunkKt = 16;    // K tiles per exact chunk (1024)
+constexpr double kRefineTail = 1e-4;
+
+__device__ __forceinline__ void oz_pair(int q, int& a, int& b, int& d) {
+  // d = a + b (slice order); the accumulator of order d
+  const int ta[kOzPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+  const int tb[kOzPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+  a = ta[q];
+  b = tb[q];
+  d = a + b;
+}
+
+// double-float helpers (hi + lo, |lo| <= ulp(hi)/2 after renormalisation)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add(float& h, float& l, float xh, float xl) {
+  float s, e;
+  two_sum(h, xh, s, e);
+  e += l + xl;
+  h = s + e;
+  l = e - (h - s);
+}
+// (ch + cl) * x as a double-float
+__device__ __forceinline__ void df_mul_f(float ch, float cl, float x, float& h, float& l) {
+  const float p = ch * x;
+  const float e = fmaf(ch, x, -p);
+  h = p;
+  l = e + cl * x;
+}
+
+struct RefineShared {
+  __nv_bfloat16* sd_img;  // kOzS slices of S_d, A operand (np rows, 2np K)
+  int* sd_exp;            // per row: exponent of the row scale
+  int* flags;             // per point: refine or not
+  size_t sd_slice;
+};
+
+// S_d (S without its entries on the pattern of B) -> Ozaki slices, one CTA per row.
+__global__ void __launch_bounds__(256) oz_pack_sd_kernel(ContourDev c, const double2* __restrict__ S, int np,
+                                                         __nv_bfloat16* __restrict__ img, size_t slice,
+                                                         int* __restrict__ exps) {
+  const int i = blockIdx.x;
+  const int kt = 2 * np / kTileK;
+  __shared__ double red[256];
+  auto val = [&](int k) -> double2 {
+    if (i >= c.n || k >= c.n) return make_double2(0.0, 0.0);
+    if (k == i || k == i - 1 || (i == 0 && k == c.n - 1)) return make_double2(0.0, 0.0);
+    return S[(size_t)i * c.n + k];
+  };
+  double m = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    const double2 z = val(k);
+    m = fmax(m, fmax(fabs(z.x), fabs(z.y)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  int e = 0;
+  if (red[0] > 0.0) frexp(red[0], &e);  // red < 2^e
+  if (threadIdx.x == 0) exps[i] = e;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    const double2 z = val(k);
+    double r[2] = {ldexp(z.x, -e), ldexp(z.y, -e)};  // |r| < 1
+    for (int sl = 0; sl < kOzS; ++sl) {
+      __nv_bfloat16 q[2];
+      for (int t = 0; t < 2; ++t) {
+        const double v = rint(ldexp(r[t], kOzBits));  // integer, |v| <= 2^kOzBits
+        q[t] = __float2bfloat16_rn((float)v);
+        r[t] = ldexp(r[t], kOzBits) - v;
+      }
+      *reinterpret_cast<__nv_bfloat162*>(img + sl * slice + img_offset(i, 2 * k, kt)) = __halves2bfloat162(q[0], q[1]);
+    }
+  }
+}
+
+// flags[q] = 1 unless q lies in the smallest-weight tail of total weight
+// <= kRefineTail * sum(w) (weights taken as w_q (1 + |eps| + |ebar|), which
+// also bounds the current's quadrature factor).  One CTA; bisection on the
+// threshold in log space.
+__global__ void __launch_bounds__(1024) refine_select_kernel(const double* __restrict__ eps,
+                                                             const double* __restrict__ ebar,
+                                                             const double* __restrict__ wq, int nq,
+                                                             int* __restrict__ flags) {
+  __shared__ double red[1024];
+  auto wt = [&](int q) { return fabs(wq[q]) * (1.0 + fabs(eps[q]) + fabs(ebar[q])); };
+  auto block_sum = [&](double v) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+  };
+  double tot = 0.0;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) tot += wt(q);
+  const double total = block_sum(tot);
+  double lo = -800.0, hi = 10.0;  // log2 of the threshold
+  for (int it = 0; it < 80; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double th = exp2(mid);
+    double part = 0.0;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      const double w = wt(q);
+      if (w <= th) part += w;
+    }
+    const double skipped = block_sum(part);
+    if (skipped <= kRefineTail * total) lo = mid; else hi = mid;
+  }
+  const double th = exp2(lo);
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) flags[q] = wt(q) > th ? 1 : 0;
+}
+
+// Per matrix: the (B - S_sp) coefficients of every row in double-float,
+// coef[b][3 i + {0,1,2}] = (diag, sub, boundary) as (re_hi, re_lo, im_hi, im_lo).
+__global__ void oz_coef_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                               const double* __restrict__ ebar_d, int q0, const double2* __restrict__ S, int np,
+                               float4* __restrict__ coef, const int* __restrict__ flags) {
+  const int b = blockIdx.y;
+  if (!flags[q0 + b]) return;
+  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    double2 d = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0), k = make_double2(0.0, 0.0);
+    if (i < c.n) {
+      d = make_double2(-S[(size_t)i * c.n + i].x, 1.0 - S[(size_t)i * c.n + i].y);
+      if (i >= 1) s = csub(b_sub(c, m, eps, ebar, i), S[(size_t)i * c.n + i - 1]);
+      if (i == 0) k = csub(b_corner(c, m, eps), S[c.n - 1]);
+    }
+    const double2 v[3] = {d, s, k};
+    for (int t = 0; t < 3; ++t) {
+      const float rh = (float)v[t].x, ih = (float)v[t].y;
+      coef[((size_t)b * np + i) * 3 + t] = make_float4(rh, (float)(v[t].x - rh), ih, (float)(v[t].y - ih));
+    }
+  }
+}
+
+// Per refined matrix: Ozaki slices of X' as the residual's B operand (rows
+// n = 2j, 2j+1; k = 2k', 2k'+1; [[re, -im], [im, re]] of X'[k'][j]) with a
+// power-of-two scale per column j, and X' hi/lo as the correction's A
+// operand.  Block (x, y): complex columns x*32 .. +31 of matrix y; tiles of
+// 32 x 32 pass through shared memory so both images are written along k.
+__global__ void __launch_bounds__(256) oz_pack_x_kernel(const float2* __restrict__ X, int np, int q0,
+                                                        const int* __restrict__ flags, __nv_bfloat16* __restrict__ ximg,
+                                                        int* __restrict__ xexp, __nv_bfloat16* __restrict__ aimg) {
+  const int b = blockIdx.y;
+  if (!flags[q0 + b]) return;
+  const int j0 = blockIdx.x * 32;
+  const float2* x = X + (size_t)b * np * np;
+  const int kt = 2 * np / kTileK;
+  const size_t xs = (size_t)2 * np * 2 * np, as = (size_t)np * 2 * np;
+  __nv_bfloat16* xi = ximg + b * kOzS * xs;
+  __nv_bfloat16* ai = aimg + b * 2 * as;
+  __shared__ float colmax[8][32];
+  __shared__ int cexp[32];
+  __shared__ float2 tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float m = 0.f;
+  for (int k = ty; k < np; k += 8) {
+    const float2 z = x[(size_t)k * np + j0 + tx];
+    m = fmaxf(m, fmaxf(fabsf(z.x), fabsf(z.y)));
+  }
+  colmax[ty][tx] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float mm = 0.f;
+    for (int g = 0; g < 8; ++g) mm = fmaxf(mm, colmax[g][threadIdx.x]);
+    int e = 0;
+    if (mm > 0.f) frexpf(mm, &e);
+    cexp[threadIdx.x] = e;
+    xexp[(size_t)b * np + j0 + threadIdx.x] = e;
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < np; k0 += 32) {
+    // coalesced load of rows k0 .. k0+31, columns j0 .. j0+31; the A image along j
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int k = k0 + rr, j = j0 + tx;
+      const float2 z = x[(size_t)k * np + j];
+      tile[rr][tx] = z;
+      __nv_bfloat16 rh, rl, ih, il;
+      split2(z.x, rh, rl);
+      split2(z.y, ih, il);
+      const size_t o = img_offset(k, 2 * j, kt);
+      *reinterpret_cast<__nv_bfloat162*>(ai + o) = __halves2bfloat162(rh, ih);
+      *reinterpret_cast<__nv_bfloat162*>(ai + as + o) = __halves2bfloat162(rl, il);
+    }
+    __syncthreads();
+    // the B image along k: thread tx takes row k0 + tx of column j0 + cc
+    for (int cc = ty; cc < 32; cc += 8) {
+      const int j = j0 + cc, k = k0 + tx;
+      const float2 z = tile[tx][cc];
+      const int e = cexp[cc];
+      float r[2] = {ldexpf(z.x, -e), ldexpf(z.y, -e)};
+      const size_t o0 = img_offset(2 * j, 2 * k, kt), o1 = img_offset(2 * j + 1, 2 * k, kt);
+      for (int sl = 0; sl < kOzS; ++sl) {
+        float q[2];
+        for (int t = 0; t < 2; ++t) {
+          q[t] = rintf(ldexpf(r[t], kOzBits));
+          r[t] = ldexpf(r[t], kOzBits) - q[t];
+        }
+        const __nv_bfloat16 re = __float2bfloat16_rn(q[0]), im = __float2bfloat16_rn(q[1]);
+        const __nv_bfloat16 nim = __float2bfloat16_rn(-q[1]);
+        *reinterpret_cast<__nv_bfloat162*>(xi + sl * xs + o0) = __halves2bfloat162(re, nim);
+        *reinterpret_cast<__nv_bfloat162*>(xi + sl * xs + o1) = __halves2bfloat162(im, re);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+struct OzParams {
+  const __nv_bfloat16* a;  // S_d slices (shared)
+  size_t a_slice;
+  const int* a_exp;        // row exponents
+  const __nv_bfloat16* b;  // X' slices per matrix
+  size_t b_batch, b_slice;
+  const int* b_exp;        // column exponents per matrix (np each)
+  const float2* X;         // X' per matrix (np x np)
+  const float4* coef;      // per matrix (np x 3)
+  const int* flags;
+  __nv_bfloat16* rimg;     // R' as the correction's B operand, hi/lo
+  size_t r_batch, r_slice;
+  ContourDev c;
+  ModelDev m;
+  const double* eps;
+  int q0, np, kt;
+  int* status;
+};
+
+constexpr int kOzStageBytes = kOzS * kTileBytes + kOzS * (kTileBytes / 2);  // 96 KB
+constexpr int kOzStages = 2;
+constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
+
+// grid (m tiles, n tiles, batch): consecutive CTAs share the B tile.
+// TMEM: two buffers of kOzS accumulators of kOzBn columns (chunk c in buffer
+// c & 1), so the epilogue drains one chunk while the next one is multiplied.
+__global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
+  const int bidx = blockIdx.z;
+  if (!p.flags[p.q0 + bidx]) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
+  uint64_t* empty = full + kOzStages;
+  uint64_t* acc_full = empty + kOzStages;  // 2 buffers
+  uint64_t* acc_empty = acc_full + 2;      // 2 buffers
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int nchunks = (p.kt + kOzChunkKt - 1) / kOzChunkKt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOzStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 128);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const __nv_bfloat16* b = p.b + bidx * p.b_batch;
+      int issued = 0;
+      for (int kt = 0; kt < p.kt; ++kt) {
+        const int s = kt % kOzStages;
+        const uint32_t ph = (kt / kOzStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) break;
+        unsigned char* st = smem + s * kOzStageBytes;
+        mbar_arrive_expect_tx(&full[s], kOzStageBytes);
+        for (int sl = 0; sl < kOzS; ++sl)
+          bulk_g2s(st + sl * kTileBytes, p.a + sl * p.a_slice + ((size_t)mt * p.kt + kt) * kTileElems, kTileBytes,
+                   &full[s]);
+        // B rows nt*64 .. +63: half (nt & 1) of image tile nt >> 1
+        for (int sl = 0; sl < kOzS; ++sl)
+          bulk_g2s(st + kOzS * kTileBytes + sl * (kTileBytes / 2),
+                   b + sl * p.b_slice + ((size_t)(nt >> 1) * p.kt + kt) * kTileElems + (nt & 1) * (kTileElems / 2),
+                   kTileBytes / 2, &full[s]);
+        issued = kt + 1;
+      }
+      for (int kt = issued - kOzStages < 0 ? 0 : issued - kOzStages; kt < issued; ++kt) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_test(&full[kt % kOzStages], (kt / kOzStages) & 1) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128, kOzBn);
+      bool ok = true;
+      for (int kt = 0; kt < p.kt; ++kt) {
+        const int ch = kt / kOzChunkKt, buf = ch & 1;
+        const bool first = (kt % kOzChunkKt) == 0;
+        if (first && ch >= 2) {
+          if (!mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+        }
+        const int s = kt % kOzStages;
+        if (!mbar_wait(&full[s], (kt / kOzStages) & 1, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * kOzStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kTileK / 16; ++kk) {
+#pragma unroll
+          for (int q = 0; q < kOzPairs; ++q) {
+            int a, b, d;
+            oz_pair(q, a, b, d);
+            const bool first_of_d = (q == 0 || q == 1 || q == 3 || q == 6);
+            const uint32_t a_addr = st + a * kTileBytes + kk * 256;
+            const uint32_t b_addr = st + kOzS * kTileBytes + b * (kTileBytes / 2) + kk * 256;
+            mma_bf16(tmem + buf * 256 + d * kOzBn, smem_desc(a_addr, 128, 1024), smem_desc(b_addr, 128, 1024), idesc,
+                     (first && kk == 0 && first_of_d) ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+        if ((kt % kOzChunkKt) == kOzChunkKt - 1 || kt == p.kt - 1) mma_commit(&acc_full[buf]);
+      }
+      if (!ok) {
+        mma_commit(&acc_full[0]);
+        mma_commit(&acc_full[1]);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int i = mt * kTileRows + row;  // output row of S_d X'
+    float hs[kOzBn], ls[kOzBn];
+#pragma unroll
+    for (int e = 0; e < kOzBn; ++e) { hs[e] = 0.f; ls[e] = 0.f; }
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int buf = ch & 1;
+      if (!mbar_wait(&acc_full[buf], (ch >> 1) & 1, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int d = 0; d < kOzS; ++d) {
+        const float sc = ldexpf(1.0f, -kOzBits * (d + 2));
+#pragma unroll
+        for (int pc = 0; pc < kOzBn / 32; ++pc) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + d * kOzBn + pc * 32, v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            float s, er;
+            two_sum(hs[pc * 32 + e], v[e] * sc, s, er);
+            hs[pc * 32 + e] = s;
+            ls[pc * 32 + e] += er;
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+    if (ok && !*abort_flag) {
+      const int n = p.c.n, np = p.np;
+      const bool sh = shifted_point(p.m, p.eps[p.q0 + bidx]);
+      const int r = (i < n && sh) ? (i == 0 ? n - 1 : i - 1) : i;  // row of R' fed by row i
+      const float2* x = p.X + (size_t)bidx * np * np;
+      const float4* cf = p.coef + (size_t)bidx * np * 3;
+      const float4 cd = cf[3 * i], cs = cf[3 * i + 1], cc = cf[3 * i + 2];
+      const int ei = p.a_exp[i];
+      const int* xe = p.b_exp + (size_t)bidx * np;
+      __nv_bfloat16* ri = p.rimg + bidx * p.r_batch;
+      const int kt = 2 * np / kTileK;
+      const int j0 = nt * (kOzBn / 2);
+#pragma unroll
+      for (int u = 0; u < kOzBn / 2; ++u) {
+        const int j = j0 + u;
+        const int sc = ei + xe[j];
+        float tr_h = ldexpf(hs[2 * u], sc), tr_l = ldexpf(ls[2 * u], sc);
+        float ti_h = ldexpf(hs[2 * u + 1], sc), ti_l = ldexpf(ls[2 * u + 1], sc);
+        // T - (B - S_sp) X' at (i, j), double-float
+        auto sub_prod = [&](float4 co, float2 xv) {
+          float h, l;
+          df_mul_f(co.x, co.y, xv.x, h, l); df_add(tr_h, tr_l, -h, -l);  // - c_re x_re
+          df_mul_f(co.z, co.w, xv.y, h, l); df_add(tr_h, tr_l, h, l);    // + c_im x_im
+          df_mul_f(co.x, co.y, xv.y, h, l); df_add(ti_h, ti_l, -h, -l);  // - c_re x_im
+          df_mul_f(co.z, co.w, xv.x, h, l); df_add(ti_h, ti_l, -h, -l);  // - c_im x_re
+        };
+        sub_prod(cd, x[(size_t)i * np + j]);
+        if (i >= 1 && i < n) sub_prod(cs, x[(size_t)(i - 1) * np + j]);
+        if (i == 0) sub_prod(cc, x[(size_t)(n - 1) * np + j]);
+        if (r == j) df_add(tr_h, tr_l, 1.0f, 0.0f);
+        const float re = tr_h + tr_l, im = ti_h + ti_l;
+        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        split2(re, rh, rl);
+        split2(im, ih, il);
+        split2(-im, nh, nl);
+        const size_t o0 = img_offset(2 * j, 2 * r, kt), o1 = img_offset(2 * j + 1, 2 * r, kt);
+        *reinterpret_cast<__nv_bfloat162*>(ri + o0) = __halves2bfloat162(rh, nh);
+        *reinterpret_cast<__nv_bfloat162*>(ri + o1) = __halves2bfloat162(ih, rh);
+        *reinterpret_cast<__nv_bfloat162*>(ri + p.r_slice + o0) = __halves2bfloat162(rl, nl);
+        *reinterpret_cast<__nv_bfloat162*>(ri + p.r_slice + o1) = __halves2bfloat162(il, rl);
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    for (int s = 0; s < 2 && s < nchunks; ++s) {
+      const int last = ((nchunks - 1 - s) / 2) * 2 + s;  // last chunk that used buffer s
+      const uint64_t t0 = global_ns();
+      while (!mbar_test(&acc_full[s], (last >> 1) & 1) && global_ns() - t0 < kWaitNs) {
+      }
+    }
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && *abort_flag && p.status) atomicCAS(p.status, 0, DS_TIMEOUT);
+}
+
+// dX' = acc (FP32 interleaved).
+struct EpiStore {
+  float* out;
+  size_t bstride;  // floats between matrices
+  int np;
+  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+    const int i = mt * kTileRows + r;
+    float* row = out + b * bstride + (size_t)i * 2 * np + nt * CfgGJ::kBn + c0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      *reinterpret_cast<float4*>(row + 4 * u) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+  }
+};
+
+// gloc (= or +=) sum_b wq (X' + flag dX')[i][col(j)] and the current, b ascending.
+__global__ void reduce_refined_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                      const double* __restrict__ wq_d, int q0, int nb, const float2* __restrict__ X,
+                                      const float2* __restrict__ dX, const int* __restrict__ flags, int np, bool first,
+                                      double2* __restrict__ gloc) {
+  const size_t total = (size_t)c.n * c.n, mat = (size_t)np * np;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / c.n), j = (int)(e % c.n);
+    double2 acc = first ? make_double2(0.0, 0.0) : gloc[e];
+    for (int b = 0; b < nb; ++b) {
+      const int q = q0 + b;
+      const size_t off = b * mat + (size_t)i * np + unshift_col(j, c.n, shifted_point(m, eps_d[q]));
+      double2 v = to_d(X[off]);
+      if (flags[q]) v = cadd(v, to_d(dX[off]));
+      acc.x = fma(wq_d[q], v.x, acc.x);
+      acc.y = fma(wq_d[q], v.y, acc.y);
+    }
+    gloc[e] = acc;
+  }
+}
+
+__global__ void reduce_refined_current_kernel(ContourDev c, ModelDev mo, const double* __restrict__ eps_d,
+                                              const double* __restrict__ ebar_d, const double* __restrict__ wq_d,
+                                              int q0, int nb, const float2* __restrict__ X,
+                                              const float2* __restrict__ dX, const int* __restrict__ flags, int np,
+                                              bool first, double2* __restrict__ jacc) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mm >= c.nt) return;
+  const double t = t_re(c, mm);
+  const int jcol = 2 * c.nt - mm;
+  const size_t mat = (size_t)np * np;
+  double2 acc = first ? make_double2(0.0, 0.0) : jacc[mm];
+  for (int b = 0; b < nb; ++b) {
+    const int q = q0 + b;
+    const double eps = eps_d[q];
+    const size_t off = b * mat + (size_t)mm * np + unshift_col(jcol, c.n, shifted_point(mo, eps));
+    double2 v = to_d(X[off]);
+    if (flags[q]) v = cadd(v, to_d(dX[off]));
+    const double w = wq_d[q] * ebar_at(t, eps, ebar_d[q], mo.E);
+    acc.x = fma(w, v.x, acc.x);
+    acc.y = fma(w, v.y, acc.y);
+  }
+  jacc[mm] = acc;
+}
+
+// Refinement buffers, each an array over the batch.
+struct RefineLayout {
+  size_t ximg, xexp, aimg, rimg, coef, dx, total;  // bytes per region
+};
+RefineLayout refine_layout(int np, int nb) {
+  RefineLayout r{};
+  r.ximg = align1k(kOzS * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * np * nb);
+  r.xexp = align1k(sizeof(int) * (size_t)np * nb);
+  r.aimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * np * nb);
+  r.rimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * np * nb);
+  r.coef = align1k(sizeof(float4) * (size_t)np * 3 * nb);
+  r.dx = align1k(sizeof(float2) * (size_t)np * np * nb);
+  r.total = r.ximg + r.xexp + r.aimg + r.rimg + r.coef + r.dx;
+  return r;
+}
+
+RefineShared shared_layout(char* shared, int np) {
+  RefineShared r{};
+  r.sd_slice = (size_t)np * 2 * np;
+  r.sd_img = reinterpret_cast<__nv_bfloat16*>(shared);
+  r.sd_exp = reinterpret_cast<int*>(shared + align1k(kOzS * sizeof(__nv_bfloat16) * r.sd_slice));
+  r.flags = reinterpret_cast<int*>(reinterpret_cast<char*>(r.sd_exp) + align1k(sizeof(int) * (size_t)np));
+  return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ lattice batch on this path
+
+size_t umma_batch_bytes_per_matrix(int np) { return gj_buffers(np).total + refine_layout(np, 1).total; }
+int umma_default_batch(int np) { return np <= 1024 ? 152 : 76; }
+size_t umma_shared_bytes(int np, int nq) {
+  return align1k(kOzS * sizeof(__nv_bfloat16) * (size_t)np * 2 * np) + align1k(sizeof(int) * (size_t)np) +
+         align1k(sizeof(int) * (size_t)nq);
+}
+size_t umma_batch_bytes(int np, int nb) { return gj_buffers(np).total * nb + refine_layout(np, nb).total; }
+
+int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
+                        const double* wq, int nq, char* shared, cudaStream_t st) {
+  RefineShared r = shared_layout(shared, np);
+  oz_pack_sd_kernel<<<np, 256, 0, st>>>(c, S, np, r.sd_img, r.sd_slice, r.sd_exp);
+  NED_LAUNCH_CHECK("oz_pack_sd_kernel");
+  refine_select_kernel<<<1, 1024, 0, st>>>(eps, ebar, wq, nq, r.flags);
+  NED_LAUNCH_CHECK("refine_select_kernel");
+  return NEDMFT_OK;
+}
+
+int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
+                       const double* wq, int q0, int nb, int np, const double2* S, char* shared, char* batch,
+                       bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
+  const GjBuffers g = gj_buffers(np);
+  const RefineShared sh = shared_layout(shared, np);
+  const int mb_alloc = nb;  // regions are sized for this batch by the caller's layout
+  (void)mb_alloc;
+  // layout: nb matrices | nb GJ panel scratch | refinement regions
+  float2* X = reinterpret_cast<float2*>(batch);
+  char* scratch = batch + g.mat * nb;
+  const size_t per = g.pimg + g.cimg + g.timg + g.rimg;
+  const RefineLayout rl = refine_layout(np, nb);
+  char* rbase = scratch + per * nb;
+  __nv_bfloat16* ximg = reinterpret_cast<__nv_bfloat16*>(rbase);
+  int* xexp = reinterpret_cast<int*>(rbase + rl.ximg);
+  __nv_bfloat16* aimg = reinterpret_cast<__nv_bfloat16*>(rbase + rl.ximg + rl.xexp);
+  __nv_bfloat16* rimg = reinterpret_cast<__nv_bfloat16*>(rbase + rl.ximg + rl.xexp + rl.aimg);
+  float4* coef = reinterpret_cast<float4*>(rbase + rl.ximg + rl.xexp + rl.aimg + rl.rimg);
+  float2* dx = reinterpret_cast<float2*>(rbase + rl.ximg + rl.xexp + rl.aimg + rl.rimg + rl.coef);
+  const size_t mat = (size_t)np * np;
+  const size_t xs = (size_t)2 * np * 2 * np, as = (size_t)np * 2 * np, rs = (size_t)2 * np * 2 * np;
+  int rc;
+  if ((rc = launch_gen_a<float>(c, m, eps, ebar, q0, nb, S, X, np, st))) return rc;
+  if ((rc = gj_blocked_umma(X, c.n, np, nb, scratch, status, st))) return rc;
+  oz_coef_kernel<<<dim3((np + 255) / 256, nb), 256, 0, st>>>(c, m, eps, ebar, q0, S, np, coef, sh.flags);
+  NED_LAUNCH_CHECK("oz_coef_kernel");
+  oz_pack_x_kernel<<<dim3(np / 32, nb), 256, 0, st>>>(X, np, q0, sh.flags, ximg, xexp, aimg);
+  NED_LAUNCH_CHECK("oz_pack_x_kernel");
+  {
+    OzParams p{};
+    p.a = sh.sd_img; p.a_slice = sh.sd_slice; p.a_exp = sh.sd_exp;
+    p.b = ximg; p.b_batch = kOzS * xs; p.b_slice = xs; p.b_exp = xexp;
+    p.X = X; p.coef = coef; p.flags = sh.flags;
+    p.rimg = rimg; p.r_batch = 2 * rs; p.r_slice = rs;
+    p.c = c; p.m = m; p.eps = eps; p.q0 = q0; p.np = np; p.kt = 2 * np / kTileK; p.status = status;
+    static bool attr = false;
+    if (!attr) {
+      NED_CUDA(cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
+      attr = true;
+    }
+    oz_residual_kernel<<<dim3(np / kTileRows, 2 * np / kOzBn, nb), 192, kOzSmem, st>>>(p);
+    NED_LAUNCH_CHECK("oz_residual_kernel");
+  }
+  {  // dX' = X' R' (bf16x3), refined points only
+    GemmParams p{aimg, 2 * as, as, rimg, 2 * rs, rs, 2 * np / kTileK, status};
+    EpiStore epi{reinterpret_cast<float*>(dx), 2 * mat, np};
+    static bool attr = false;
+    if (!attr) {
+      NED_CUDA(cudaFuncSetAttribute(umma_gemm_flag_kernel<CfgGJ, Split3, EpiStore>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, CfgGJ::kSmem));
+      attr = true;
+    }
+    umma_gemm_flag_kernel<CfgGJ, Split3, EpiStore>
+        <<<dim3(2 * np / CfgGJ::kBn, np / kTileRows, nb), 192, CfgGJ::kSmem, st>>>(p, epi, sh.flags, q0);
+    NED_LAUNCH_CHECK("umma_gemm_flag_kernel");
+  }
+  {
+    const size_t total = (size_t)c.n * c.n;
+    int bx = (int)((total + 255) / 256);
+    if (bx > 152 * 8) bx = 152 * 8;
+    reduce_refined_kernel<<<bx, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dx, sh.flags, np, first, gloc);
+    NED_LAUNCH_CHECK("reduce_refined_kernel");
+    if (jacc) {
+      reduce_refined_current_kernel<<<ceil_div(c.nt, 128), 128, 0, st>>>(c, m, eps, ebar, wq, q0, nb, X, dx,
+                                                                         sh.flags, np, first, jacc);
+      NED_LAUNCH_CHECK("reduce_refined_current_kernel");
+    }
+  }
+  return NEDMFT_OK;
 }
 
 }  // namespace nedmft

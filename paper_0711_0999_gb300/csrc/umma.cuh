@@ -7,9 +7,11 @@
 namespace nedmft {
 
 size_t umma_batch_bytes_per_matrix(int np);
+size_t umma_batch_bytes(int np, int nb);
 int umma_default_batch(int np);
-size_t umma_shared_bytes(int np);
-int umma_prepare_shared(const ContourDev& c, const double2* S, int np, char* shared, cudaStream_t st);
+size_t umma_shared_bytes(int np, int nq);
+int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
+                        const double* wq, int nq, char* shared, cudaStream_t st);
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
                        const double* wq, int q0, int nb, int np, const double2* S, char* shared, char* batch,
                        bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st);
