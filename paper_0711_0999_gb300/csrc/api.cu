@@ -31,7 +31,7 @@ Path choose_path(const nedmft_contour& c, nedmft_precision p) {
 
 int default_batch(const nedmft_contour& c, int nq, Path path) {
   const size_t np = padded(c.n_c);
-  size_t per = 0, budget = (size_t)16 << 30;  // about 16 GB of batch buffers
+  size_t per = 0, budget = (size_t)40 << 30;  // about 40 GB of batch buffers
   int cap = 152;
   switch (path) {
     case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
@@ -160,7 +160,7 @@ int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* s
         break;
       }
       case Path::MixedUmma: {
-        if ((rc = umma_lattice_batch(cd, md, eps, ebar, wq, q0, nb, np, S, extra, batch, first, gloc, ja, status, st)))
+        if ((rc = umma_lattice_batch(cd, md, eps, ebar, wq, q0, nb, nq, np, S, extra, batch, first, gloc, ja, status, st)))
           return rc;
         break;
       }

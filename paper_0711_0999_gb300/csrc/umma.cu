@@ -254,59 +254,78 @@ struct EpiRPack {
 
 // P = inv(A_KK) (kNb x kNb, FP32, no pivoting -- the static row order makes
 // the pivots safe) written as the R-product's A operand: row r, k = 2c / 2c+1.
-__global__ void __launch_bounds__(512) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
-                                                            __nv_bfloat16* __restrict__ pimg, size_t pstride,
-                                                            size_t pslice, int* status) {
-  extern __shared__ float2 sp[];
-  constexpr int ld = kNb + 1;
-  float2* a = sp;
-  float2* col = sp + kNb * ld;
+// 1024 threads, each holding a 4 x 4 block of A_KK in registers; step k
+// broadcasts row k and column k through double-buffered shared memory.
+__global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
+                                                             __nv_bfloat16* __restrict__ pimg, size_t pstride,
+                                                             size_t pslice, int* status) {
+  __shared__ float2 rowb[2][kNb], colb[2][kNb];
   const int b = blockIdx.x;
+  const int t = threadIdx.x;
+  const int r0 = 4 * (t >> 5), c0 = 4 * (t & 31);
   const float2* src = A + (size_t)b * np * np;
-  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
-    const int r = e / kNb, c = e % kNb;
-    a[r * ld + c] = src[(size_t)(k0 + r) * np + k0 + c];
+  float2 a[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4* p = reinterpret_cast<const float4*>(src + (size_t)(k0 + r0 + i) * np + k0 + c0);
+    const float4 u = p[0], v = p[1];
+    a[i][0] = make_float2(u.x, u.y); a[i][1] = make_float2(u.z, u.w);
+    a[i][2] = make_float2(v.x, v.y); a[i][3] = make_float2(v.z, v.w);
   }
-  __syncthreads();
+  bool bad = false;
   for (int k = 0; k < kNb; ++k) {
-    if (threadIdx.x < kNb) col[threadIdx.x] = a[threadIdx.x * ld + k];
+    const int buf = k & 1;
+    if ((k >> 2) == (r0 >> 2)) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (r0 + i == k)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) rowb[buf][c0 + j] = a[i][j];
+    }
+    if ((k >> 2) == (c0 >> 2)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (c0 + j == k)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) colb[buf][r0 + i] = a[i][j];
+    }
     __syncthreads();
     float2 pinv;
-    const bool ok = cinv_guard<float>(col[k], pinv, 1e-6f);
-    if (!ok && threadIdx.x == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
-    if (threadIdx.x < kNb) {
-      const int t = threadIdx.x;
-      a[k * ld + t] = (t == k) ? pinv : cmul(a[k * ld + t], pinv);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
-      const int i = e / kNb, j = e % kNb;
-      if (i == k) continue;
-      const float2 f = col[i];
-      if (j == k) {
-        const float2 w = cmul(f, pinv);
-        a[i * ld + k] = make_float2(-w.x, -w.y);
-      } else {
-        const float2 rk = a[k * ld + j];
-        float2 w = a[i * ld + j];
-        w.x -= f.x * rk.x - f.y * rk.y;
-        w.y -= f.x * rk.y + f.y * rk.x;
-        a[i * ld + j] = w;
+    bad |= !cinv_guard<float>(rowb[buf][k], pinv, 1e-6f);
+    float2 rk[4], g[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) rk[j] = rowb[buf][c0 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = cmul(colb[buf][r0 + i], pinv);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + i, c = c0 + j;
+        if (r == k) {
+          a[i][j] = (c == k) ? pinv : cmul(rk[j], pinv);
+        } else if (c == k) {
+          a[i][j] = make_float2(-g[i].x, -g[i].y);
+        } else {
+          a[i][j].x -= g[i].x * rk[j].x - g[i].y * rk[j].y;
+          a[i][j].y -= g[i].x * rk[j].y + g[i].y * rk[j].x;
+        }
       }
     }
-    __syncthreads();
   }
+  if (bad && t == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
   __nv_bfloat16* dst = pimg + b * pstride;
-  for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
-    const int r = e / kNb, c = e % kNb;
-    const float2 z = a[r * ld + c];
-    __nv_bfloat16 rh, rl, ih, il;
-    split2(z.x, rh, rl);
-    split2(z.y, ih, il);
-    const size_t o = img_offset(r, 2 * c, kKt);
-    *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
-    *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
-  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat16 rh, rl, ih, il;
+      split2(a[i][j].x, rh, rl);
+      split2(a[i][j].y, ih, il);
+      const size_t o = img_offset(r0 + i, 2 * (c0 + j), kKt);
+      *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
+      *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
+    }
 }
 
 // Block x of matrix y: rows x*128 .. +127 of C' (the update's A operand) and
@@ -389,14 +408,8 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
   const size_t pstride = per / 2, pslice = (size_t)kNb * 2 * kNb;
   const size_t cslice = (size_t)np * 2 * kNb;
   const size_t tslice = (size_t)2 * np * 2 * kNb;
-  const size_t smem_piv = sizeof(float2) * (kNb * (kNb + 1) + kNb);
-  static bool attr = false;
-  if (!attr) {
-    NED_CUDA(cudaFuncSetAttribute(gj_pivot_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_piv));
-    attr = true;
-  }
   for (int k0 = 0; k0 < np; k0 += kNb) {
-    gj_pivot_pack_kernel<<<nb, 512, smem_piv, st>>>(A, np, k0, pimg, pstride, pslice, status);
+    gj_pivot_pack_kernel<<<nb, 1024, 0, st>>>(A, np, k0, pimg, pstride, pslice, status);
     NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
     gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, k0, cimg, pstride, cslice, timg, pstride, tslice);
     NED_LAUNCH_CHECK("gj_panel_pack_kernel");
@@ -477,6 +490,7 @@ struct RefineShared {
   __nv_bfloat16* sd_img;  // kOzS slices of S_d, A operand (np rows, 2np K)
   int* sd_exp;            // per row: exponent of the row scale
   int* flags;             // per point: refine or not
+  float2* base;           // -S in FP32, identity padding (np x np)
   size_t sd_slice;
 };
 
@@ -581,6 +595,53 @@ __global__ void oz_coef_kernel(ContourDev c, ModelDev m, const double* __restric
       const float rh = (float)v[t].x, ih = (float)v[t].y;
       coef[((size_t)b * np + i) * 3 + t] = make_float4(rh, (float)(v[t].x - rh), ih, (float)(v[t].y - ih));
     }
+  }
+}
+
+// A'_b = P (B_q - S) in FP32 from the shared base -S (np x np, identity
+// padding): row r copies base row i = sigma(r) and adds the three entries of
+// B_q in row i.  One block per (row, matrix).
+__global__ void __launch_bounds__(128) gen_a_fast_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+                                                         const double* __restrict__ ebar_d, int q0,
+                                                         const float2* __restrict__ base, float2* __restrict__ A,
+                                                         int np) {
+  const int r = blockIdx.x, b = blockIdx.y;
+  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+  __shared__ float2 bv[3];
+  __shared__ int bc[3];
+  int i = r;
+  if (r < c.n && shifted_point(m, eps)) i = (r + 1 == c.n) ? 0 : r + 1;
+  if (threadIdx.x == 0) {
+    bc[0] = bc[1] = bc[2] = -1;
+    if (i < c.n) {
+      bc[0] = i;
+      bv[0] = make_float2(0.f, 1.f);
+      if (i >= 1) { const double2 z = b_sub(c, m, eps, ebar, i); bc[1] = i - 1; bv[1] = make_float2((float)z.x, (float)z.y); }
+      if (i == 0 && c.n > 1) { const double2 z = b_corner(c, m, eps); bc[2] = c.n - 1; bv[2] = make_float2((float)z.x, (float)z.y); }
+    }
+  }
+  __syncthreads();
+  const float4* src = reinterpret_cast<const float4*>(base + (size_t)i * np);
+  float4* dst = reinterpret_cast<float4*>(A + (size_t)b * np * np + (size_t)r * np);
+  for (int v = threadIdx.x; v < np / 2; v += blockDim.x) {
+    float4 x = src[v];
+    const int ja = 2 * v, jb = 2 * v + 1;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      if (bc[e] == ja) { x.x += bv[e].x; x.y += bv[e].y; }
+      if (bc[e] == jb) { x.z += bv[e].x; x.w += bv[e].y; }
+    }
+    dst[v] = x;
+  }
+}
+
+__global__ void base_neg_s_kernel(ContourDev c, const double2* __restrict__ S, float2* __restrict__ base, int np) {
+  const int r = blockIdx.x;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    float2 v;
+    if (r < c.n && j < c.n) { const double2 z = S[(size_t)r * c.n + j]; v = make_float2((float)-z.x, (float)-z.y); }
+    else v = make_float2(r == j ? 1.f : 0.f, 0.f);
+    base[(size_t)r * np + j] = v;
   }
 }
 
@@ -881,25 +942,55 @@ struct EpiStore {
   }
 };
 
-// gloc (= or +=) sum_b wq (X' + flag dX')[i][col(j)] and the current, b ascending.
-__global__ void reduce_refined_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
-                                      const double* __restrict__ wq_d, int q0, int nb, const float2* __restrict__ X,
-                                      const float2* __restrict__ dX, const int* __restrict__ flags, int np, bool first,
-                                      double2* __restrict__ gloc) {
-  const size_t total = (size_t)c.n * c.n, mat = (size_t)np * np;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / c.n), j = (int)(e % c.n);
-    double2 acc = first ? make_double2(0.0, 0.0) : gloc[e];
-    for (int b = 0; b < nb; ++b) {
-      const int q = q0 + b;
-      const size_t off = b * mat + (size_t)i * np + unshift_col(j, c.n, shifted_point(m, eps_d[q]));
-      double2 v = to_d(X[off]);
-      if (flags[q]) v = cadd(v, to_d(dX[off]));
-      acc.x = fma(wq_d[q], v.x, acc.x);
-      acc.y = fma(wq_d[q], v.y, acc.y);
-    }
-    gloc[e] = acc;
+// gloc (= or +=) sum_b wq (X' + flag dX')[i][col(j)], b ascending.  The sum
+// runs in double-float (hi + lo FP32 pairs); w_q is split into hi + lo and
+// X' is exact in FP32, so w_q X' is formed exactly (two-product).
+constexpr int kRedMaxBatch = 512;
+__global__ void __launch_bounds__(256) reduce_refined_kernel(ContourDev c, ModelDev m,
+                                                             const double* __restrict__ eps_d,
+                                                             const double* __restrict__ wq_d, int q0, int nb,
+                                                             const float2* __restrict__ X,
+                                                             const float2* __restrict__ dX,
+                                                             const int* __restrict__ flags, int np, bool first,
+                                                             double2* __restrict__ gloc) {
+  __shared__ float wh[kRedMaxBatch], wl[kRedMaxBatch];
+  __shared__ unsigned char shf[kRedMaxBatch], rf[kRedMaxBatch];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const double w = wq_d[q0 + b];
+    wh[b] = (float)w;
+    wl[b] = (float)(w - (double)wh[b]);
+    shf[b] = shifted_point(m, eps_d[q0 + b]) ? 1 : 0;
+    rf[b] = flags[q0 + b] ? 1 : 0;
   }
+  __syncthreads();
+  const size_t total = (size_t)c.n * c.n, mat = (size_t)np * np;
+  const int row_blocks = c.n;
+  for (int i = blockIdx.x; i < row_blocks; i += gridDim.x) {
+    for (int j = threadIdx.x; j < c.n; j += blockDim.x) {
+      const size_t e = (size_t)i * c.n + j;
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      const int j0 = j, j1 = (j == 0 ? c.n - 1 : j - 1);
+      for (int b = 0; b < nb; ++b) {
+        const size_t off = b * mat + (size_t)i * np + (shf[b] ? j1 : j0);
+        const float2 x = X[off];
+        const float h = wh[b], l = wl[b];
+        float px = h * x.x, ex = fmaf(h, x.x, -px) + l * x.x;
+        float py = h * x.y, ey = fmaf(h, x.y, -py) + l * x.y;
+        if (rf[b]) {
+          const float2 d = dX[off];
+          ex += h * d.x;
+          ey += h * d.y;
+        }
+        df_add(rh, rl, px, ex);
+        df_add(ih, il, py, ey);
+      }
+      double2 acc = first ? make_double2(0.0, 0.0) : gloc[e];
+      acc.x += (double)rh + (double)rl;
+      acc.y += (double)ih + (double)il;
+      gloc[e] = acc;
+    }
+  }
+  (void)total;
 }
 
 __global__ void reduce_refined_current_kernel(ContourDev c, ModelDev mo, const double* __restrict__ eps_d,
@@ -942,30 +1033,34 @@ RefineLayout refine_layout(int np, int nb) {
   return r;
 }
 
-RefineShared shared_layout(char* shared, int np) {
+RefineShared shared_layout(char* shared, int np, int nq) {
   RefineShared r{};
   r.sd_slice = (size_t)np * 2 * np;
   r.sd_img = reinterpret_cast<__nv_bfloat16*>(shared);
   r.sd_exp = reinterpret_cast<int*>(shared + align1k(kOzS * sizeof(__nv_bfloat16) * r.sd_slice));
   r.flags = reinterpret_cast<int*>(reinterpret_cast<char*>(r.sd_exp) + align1k(sizeof(int) * (size_t)np));
+  r.base = reinterpret_cast<float2*>(reinterpret_cast<char*>(r.flags) + align1k(sizeof(int) * (size_t)nq));
   return r;
 }
+size_t flags_bytes(int nq) { return align1k(sizeof(int) * (size_t)nq); }
 
 }  // namespace
 
 // ------------------------------------------------------------------ lattice batch on this path
 
 size_t umma_batch_bytes_per_matrix(int np) { return gj_buffers(np).total + refine_layout(np, 1).total; }
-int umma_default_batch(int np) { return np <= 1024 ? 152 : 76; }
+int umma_default_batch(int np) { return np <= 2048 ? 152 : 76; }
 size_t umma_shared_bytes(int np, int nq) {
   return align1k(kOzS * sizeof(__nv_bfloat16) * (size_t)np * 2 * np) + align1k(sizeof(int) * (size_t)np) +
-         align1k(sizeof(int) * (size_t)nq);
+         flags_bytes(nq) + align1k(sizeof(float2) * (size_t)np * np);
 }
 size_t umma_batch_bytes(int np, int nb) { return gj_buffers(np).total * nb + refine_layout(np, nb).total; }
 
 int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
                         const double* wq, int nq, char* shared, cudaStream_t st) {
-  RefineShared r = shared_layout(shared, np);
+  RefineShared r = shared_layout(shared, np, nq);
+  base_neg_s_kernel<<<np, 256, 0, st>>>(c, S, r.base, np);
+  NED_LAUNCH_CHECK("base_neg_s_kernel");
   oz_pack_sd_kernel<<<np, 256, 0, st>>>(c, S, np, r.sd_img, r.sd_slice, r.sd_exp);
   NED_LAUNCH_CHECK("oz_pack_sd_kernel");
   refine_select_kernel<<<1, 1024, 0, st>>>(eps, ebar, wq, nq, r.flags);
@@ -974,10 +1069,10 @@ int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const dou
 }
 
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
-                       const double* wq, int q0, int nb, int np, const double2* S, char* shared, char* batch,
-                       bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
+                       const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
+                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
   const GjBuffers g = gj_buffers(np);
-  const RefineShared sh = shared_layout(shared, np);
+  const RefineShared sh = shared_layout(shared, np, nq_total);
   const int mb_alloc = nb;  // regions are sized for this batch by the caller's layout
   (void)mb_alloc;
   // layout: nb matrices | nb GJ panel scratch | refinement regions
@@ -995,7 +1090,8 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
   const size_t mat = (size_t)np * np;
   const size_t xs = (size_t)2 * np * 2 * np, as = (size_t)np * 2 * np, rs = (size_t)2 * np * 2 * np;
   int rc;
-  if ((rc = launch_gen_a<float>(c, m, eps, ebar, q0, nb, S, X, np, st))) return rc;
+  gen_a_fast_kernel<<<dim3(np, nb), 128, 0, st>>>(c, m, eps, ebar, q0, sh.base, X, np);
+  NED_LAUNCH_CHECK("gen_a_fast_kernel");
   if ((rc = gj_blocked_umma(X, c.n, np, nb, scratch, status, st))) return rc;
   oz_coef_kernel<<<dim3((np + 255) / 256, nb), 256, 0, st>>>(c, m, eps, ebar, q0, S, np, coef, sh.flags);
   NED_LAUNCH_CHECK("oz_coef_kernel");
@@ -1033,7 +1129,9 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
     const size_t total = (size_t)c.n * c.n;
     int bx = (int)((total + 255) / 256);
     if (bx > 152 * 8) bx = 152 * 8;
-    reduce_refined_kernel<<<bx, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dx, sh.flags, np, first, gloc);
+    if (nb > kRedMaxBatch) return set_error(NEDMFT_EINVAL, "reduce: batch %d > %d", nb, kRedMaxBatch);
+    reduce_refined_kernel<<<c.n < 152 * 8 ? c.n : 152 * 8, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dx, sh.flags, np,
+                                                                       first, gloc);
     NED_LAUNCH_CHECK("reduce_refined_kernel");
     if (jacc) {
       reduce_refined_current_kernel<<<ceil_div(c.nt, 128), 128, 0, st>>>(c, m, eps, ebar, wq, q0, nb, X, dx,

@@ -13,7 +13,7 @@ size_t umma_shared_bytes(int np, int nq);
 int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
                         const double* wq, int nq, char* shared, cudaStream_t st);
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
-                       const double* wq, int q0, int nb, int np, const double2* S, char* shared, char* batch,
-                       bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st);
+                       const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
+                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st);
 
 }  // namespace nedmft
