@@ -188,6 +188,32 @@ int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
                    nedmft_precision prec, double* j_d, double* j_imag_d,
                    void* ws_d, size_t ws_bytes, void* stream);
 
+/* The lattice step for small contours (n_c <= 112), FP64 arithmetic, with
+ * no workspace argument and no device allocation of any kind.  The paper has
+ * no counterpart to this entry point: it exists for callers that cannot
+ * allocate device memory -- for example a host physics code that manages all
+ * device memory itself and only hands this library its input and output
+ * buffers, or a plugin running under a framework whose caching allocator owns
+ * the device and exposes no raw workspace to it.
+ *   Arguments and results are those of nedmft_lattice_gloc with prec =
+ *   NEDMFT_FP64 (points are inverted 32 at a time).
+ *   Scratch: a fixed device array of about 6.6 MB inside the library, one
+ *   per GPU that loads the library, held until the process exits.  The
+ *   first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it.
+ *   Calls share the array: two calls whose work overlaps on the GPU (on
+ *   different streams, or from different host threads) race and corrupt each
+ *   other's results.  Every scratch byte a call reads was written earlier in
+ *   the same call, so nothing needs clearing between calls.
+ *   Errors: NEDMFT_EINVAL for n_c > 112, nq < 1, a NULL pointer or an invalid
+ *   contour (message in nedmft_last_error); NEDMFT_ECUDA if the address
+ *   lookup or a launch fails.  Stream-ordered. */
+int nedmft_lattice_gloc_static(const nedmft_contour* c, const nedmft_model* m,
+                               const nedmft_c128* sigma_d, const double* eps_d,
+                               const double* ebar_d, const double* wq_d,
+                               int32_t nq, nedmft_c128* gloc_d, double* j_d,
+                               double* j_imag_d, void* stream);
+
 /* ---------------------------------------------------------------- impurity */
 
 /* Workspace bytes for nedmft_impurity_update. */

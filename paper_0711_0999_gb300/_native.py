@@ -69,6 +69,8 @@ SIGNATURES = {
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nedmft_current": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_int,
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nedmft_lattice_gloc_static": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                                  c_void_p, c_void_p, c_void_p, c_void_p]),
     "nedmft_impurity_workspace_size": (c_size_t, [PC]),
     "nedmft_impurity_update": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                               c_void_p]),
