@@ -198,6 +198,168 @@ int launch_gemm(const GemmParams& p, int n_tiles, int m_tiles, int batch, const 
 
 using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (192 KB)
 
+// Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear order
+// (batch, m tile, n tile), n fastest.  The stage ring runs on across tiles and
+// the TMEM holds two accumulators, so the epilogue of one tile overlaps the
+// loads and products of the next.  Epi::prefetch(b, mt, nt) may warm L2 for
+// the epilogue's own reads.
+template <class C, class Pairs, class Epi, int EPIW>
+__global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel(GemmParams p, Epi epi, int n_tiles,
+                                                                                 int m_tiles, int batch) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* acc_full = empty + C::kStages;  // 2
+  uint64_t* acc_empty = acc_full + 2;       // 2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = n_tiles * m_tiles * batch;
+  const int G = gridDim.x;
+  constexpr uint32_t kCols = 2 * C::kBn;  // two accumulators
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 32 * EPIW);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += G) {
+        const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
+        const int mt = rem / n_tiles, nt = rem % n_tiles;
+        epi.prefetch(b, mt, nt);
+        const __nv_bfloat16* a = p.a + b * p.a_batch;
+        const __nv_bfloat16* bb = p.b + b * p.b_batch;
+        for (int kt = 0; kt < p.kt; ++kt, ++it) {
+          const int s = it % C::kStages;
+          const uint32_t ph = (it / C::kStages) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) { ok = false; break; }
+          unsigned char* st = smem + s * C::kStageBytes;
+          mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+          for (int sa = 0; sa < C::kSa; ++sa)
+            bulk_g2s(st + sa * kTileBytes, a + sa * p.a_slice + ((size_t)mt * p.kt + kt) * kTileElems, kTileBytes,
+                     &full[s]);
+          for (int sb = 0; sb < C::kSb; ++sb)
+            for (int u = 0; u < C::kBTiles; ++u)
+              bulk_g2s(st + (C::kSa + sb * C::kBTiles + u) * kTileBytes,
+                       bb + sb * p.b_slice + ((size_t)(nt * C::kBTiles + u) * p.kt + kt) * kTileElems, kTileBytes,
+                       &full[s]);
+        }
+      }
+      // no copy may be left in flight at exit
+      for (int k = it - C::kStages < 0 ? 0 : it - C::kStages; k < it; ++k) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_test(&full[k % C::kStages], (k / C::kStages) & 1) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += G, ++lt) {
+        const int buf = lt & 1;
+        if (lt >= 2) {
+          if (!mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+        }
+        const uint32_t d = tmem + buf * C::kBn;
+        for (int kt = 0; kt < p.kt; ++kt, ++it) {
+          const int s = it % C::kStages;
+          if (!mbar_wait(&full[s], (it / C::kStages) & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < kTileK / 16; ++kk) {
+#pragma unroll
+            for (int q = 0; q < Pairs::kPairs; ++q) {
+              const uint32_t a_addr = st + Pairs::a(q) * kTileBytes + kk * 256;
+              const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * C::kBTiles) * kTileBytes + kk * 256;
+              mma_bf16(d, smem_desc(a_addr, 128, 1024), smem_desc(b_addr, 128, 1024), idesc,
+                       (kt > 0 || kk > 0 || q > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    // EPIW epilogue warps: warp w owns TMEM lanes 32 (w % 4) .. +31 and one of
+    // EPIW / 4 column ranges of the tile
+    const int q = warp & 3;
+    const int part = (warp - 2) >> 2;
+    constexpr int kParts = EPIW / 4;
+    constexpr int kSpan = C::kBn / kParts;
+    const int row = q * 32 + lane;
+    int lt = 0;
+    for (int t = blockIdx.x; t < total; t += G, ++lt) {
+      const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
+      const int mt = rem / n_tiles, nt = rem % n_tiles;
+      const int buf = lt & 1;
+      if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int c0 = part * kSpan; c0 < (part + 1) * kSpan; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
+        epi(b, mt, nt, row, c0, v);
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && p.status) atomicCAS(p.status, 0, DS_TIMEOUT);
+}
+
+template <class C, class Pairs, int EPIW, class Epi>
+int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
+  const int smem_bytes = C::kSmem;
+  static bool attr = false;
+  if (!attr) {
+    NED_CUDA(cudaFuncSetAttribute(umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+    attr = true;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    NED_CUDA(cudaGetDevice(&dev));
+    NED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int total = n_tiles * m_tiles * batch;
+  const int grid = total < sms ? total : sms;
+  umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>
+      <<<grid, 64 + 32 * EPIW, smem_bytes, st>>>(p, epi, n_tiles, m_tiles, batch);
+  NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
+  return NEDMFT_OK;
+}
+
+
+
 // ------------------------------------------------------------------ epilogues
 
 // A <- A(rows K and columns K zeroed) - acc, A interleaved FP32 (row stride 2 np floats).
@@ -205,20 +367,31 @@ struct EpiUpdate {
   float* A;
   size_t bstride;  // floats between matrices
   int np, k0;
+  // warm L2 with the tile's 128 rows of old values (1 KB each)
+  __device__ void prefetch(int b, int mt, int nt) const {
+    const float* base = A + b * bstride + (size_t)(mt * kTileRows) * 2 * np + nt * CfgGJ::kBn;
+    for (int r = 0; r < kTileRows; ++r)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + (size_t)r * 2 * np),
+                   "r"((uint32_t)(CfgGJ::kBn * sizeof(float)))
+                   : "memory");
+  }
   __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
     const int i = mt * kTileRows + r;
     const int n0 = nt * CfgGJ::kBn + c0;  // real column
     float* row = A + b * bstride + (size_t)i * 2 * np + n0;
     const bool ik = (i >= k0 && i < k0 + kNb);
     const int j0 = n0 >> 1;  // first complex column of the chunk
+    float4 o[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      o[u] = ik ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      float4 o = ik ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
       const int ja = j0 + 2 * u;
-      if (ja >= k0 && ja < k0 + kNb) { o.x = 0.f; o.y = 0.f; }
-      if (ja + 1 >= k0 && ja + 1 < k0 + kNb) { o.z = 0.f; o.w = 0.f; }
-      o.x -= v[4 * u]; o.y -= v[4 * u + 1]; o.z -= v[4 * u + 2]; o.w -= v[4 * u + 3];
-      *reinterpret_cast<float4*>(row + 4 * u) = o;
+      if (ja >= k0 && ja < k0 + kNb) { o[u].x = 0.f; o[u].y = 0.f; }
+      if (ja + 1 >= k0 && ja + 1 < k0 + kNb) { o[u].z = 0.f; o[u].w = 0.f; }
+      o[u].x -= v[4 * u]; o[u].y -= v[4 * u + 1]; o[u].z -= v[4 * u + 2]; o[u].w -= v[4 * u + 3];
+      *reinterpret_cast<float4*>(row + 4 * u) = o[u];
     }
   }
 };
@@ -229,6 +402,7 @@ struct EpiRPack {
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 kNb)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
+  __device__ void prefetch(int, int, int) const {}
   __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
     __nv_bfloat16* base = img + b * bstride;
     const int n0 = nt * CfgGJ::kBn + c0;
@@ -416,14 +590,14 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
     {  // R = P A_{K,:}, 128 x 2np, K = 256
       GemmParams p{pimg, pstride, pslice, timg, pstride, tslice, kKt, status};
       EpiRPack epi{rimg, pstride, tslice};
-      int rc = launch_gemm<CfgGJ, Split3>(p, 2 * np / CfgGJ::kBn, 1, nb, epi, st);
+      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, 1, nb, epi, st);
       if (rc) return rc;
     }
     {  // A <- A - C' R, np x 2np, K = 256
       GemmParams p{cimg, pstride, cslice, rimg, pstride, tslice, kKt, status};
       EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0};
       const int slot = instr_begin(st);
-      int rc = launch_gemm<CfgGJ, Split3>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
+      int rc = launch_gemm_persistent<CfgGJ, Split3, 8>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
       const int live = n - k0 < kNb ? (n - k0 > 0 ? n - k0 : 0) : kNb;
       instr_end(slot, st, 8.0 * (double)n * n * live * nb);
