@@ -161,13 +161,17 @@ def load_peaks():
         "fallback"
 
 
-def roofline_for(precision: str, tflops: float, peaks, src: str, clocks):
+def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str, clocks):
     if precision == "mixed_bf16":
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                "traffic": None, "peak_source": f"bf16 dense sustained, {src}",
-                "note": "achieved counts the algorithmic 8 N_c^2 nb flops of each rank-nb step once; "
-                        "the kernel issues 3 bf16 products per flop (hi*hi + hi*lo + lo*hi)"}
+        # arithmetic intensity of a rank-128 update: 8 N^2 128 flops per 2 N^2 8 B of
+        # FP32 complex traffic = 64 flop/B (192 issued bf16 flop/B), below the
+        # sustained bf16 / HBM balance (~263 flop/B): the kernel is HBM-bound
+        peak = peaks["hbm_gbs"]
+        tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "peak_source": f"HBM copy bandwidth, {src}",
+                "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                           "note": "algorithmic 8 N_c^2 nb flops per rank-nb step; 3 bf16 products issued per flop"}}
     mhz = peaks.get("sm_max_mhz", 2070.0)
     if precision == "mixed_fp32":
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
@@ -175,7 +179,7 @@ def roofline_for(precision: str, tflops: float, peaks, src: str, clocks):
                 "traffic": None, "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
     peak = 1.25  # nominal FP64 rate of the part
     return {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-            "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s"}
+            "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s", "hbm_gbs": gbs}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -282,8 +286,9 @@ def main():
     timed = N.ctypes.c_int64(0)
     tms = N.c_double(0.0)
     tfl = N.c_double(0.0)
+    tby = N.c_double(0.0)
     lib.nedmft_instrument_read(N.ctypes.byref(launches), N.ctypes.byref(timed), N.ctypes.byref(tms),
-                               N.ctypes.byref(tfl))
+                               N.ctypes.byref(tfl), N.ctypes.byref(tby))
     lib.nedmft_instrument(0, 0)
     clk = clocks.stop()
     api.check_status()
@@ -298,6 +303,7 @@ def main():
     flops_bform = 8.0 * n ** 3 * nq
     tflops_step = flops_bform / (ms_per_step / 1e3) / 1e12
     kern_tflops = (tfl.value / (tms.value / 1e3) / 1e12) if tms.value > 0 else 0.0
+    kern_gbs = (tby.value / (tms.value / 1e3) / 1e9) if tms.value > 0 else 0.0
 
     # end to end through the public API with host buffers
     e2e = None
@@ -338,9 +344,11 @@ def main():
                "d2h_bytes_per_step": d2h}
 
     peaks, src = load_peaks()
-    roof = roofline_for(prec, kern_tflops, peaks, src, clk)
+    roof = roofline_for(prec, kern_tflops, kern_gbs, peaks, src, clk)
     roof["kernel"] = "Gauss-Jordan trailing update"
     roof["launches_timed"] = int(timed.value)
+    roof["ms_per_launch"] = tms.value / max(1, int(timed.value))
+    roof["share_of_step"] = tms.value / ms if ms > 0 else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

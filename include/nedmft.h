@@ -109,11 +109,13 @@ int nedmft_instrument(int enable, int timing);
 
 /* Read the counters: kernel launches since nedmft_instrument(1, .), the
  * number of timed (trailing-update) launches, their summed event time in
- * milliseconds, and their summed algorithmic work in real flops
- * (8 n_c^2 nb per matrix for a rank-nb Gauss-Jordan step, the complex
- * multiply-add counted as 8 real flops).  Synchronises on the recorded
- * events.  Any output pointer may be NULL. */
-int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches, double* timed_ms, double* timed_flops);
+ * milliseconds, their summed algorithmic work in real flops (8 n_c^2 nb per
+ * matrix for a rank-nb Gauss-Jordan step, the complex multiply-add counted
+ * as 8 real flops) and their summed algorithmic DRAM bytes (one read and one
+ * write of each n_c x n_c working matrix: 2 n_c^2 times its element size).
+ * Synchronises on the recorded events.  Any output pointer may be NULL. */
+int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches, double* timed_ms, double* timed_flops,
+                           double* timed_bytes);
 
 /* ---------------------------------------------------------------- grid */
 

@@ -59,7 +59,8 @@ SIGNATURES = {
     "nedmft_version": (ctypes.c_char_p, []),
     "nedmft_check_status": (ctypes.c_int, [c_void_p]),
     "nedmft_instrument": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
-    "nedmft_instrument_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), PD, PD]),
+    "nedmft_instrument_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), PD, PD,
+                                               PD]),
     "nedmft_contour_grid": (ctypes.c_int, [c_double, c_double, c_double, c_double, c_double, PC, c_void_p, c_void_p]),
     "nedmft_gauss_hermite": (ctypes.c_int, [c_int32, PD, PD]),
     "nedmft_quadrature_grid": (ctypes.c_int, [c_int32, PD, PD, PD]),

@@ -35,7 +35,7 @@ int cuda_fail(cudaError_t e, const char* what);
 void instr_count();
 bool instr_timing();
 int instr_begin(cudaStream_t st);                       // returns a slot, or -1
-void instr_end(int slot, cudaStream_t st, double flops);  // flops: algorithmic work of the launch
+void instr_end(int slot, cudaStream_t st, double flops, double bytes);  // algorithmic work of the launch
 
 // Device status word (one per device, file-scope in status.cu).  Kernels
 // record the first failure with atomicCAS; nedmft_check_status reads it.

@@ -319,7 +319,8 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
     gj_update_kernel<T, NB><<<dim3(np / 64, np / 64, nb_batch), 256, smem, st>>>(A, np, k0, Rbuf, Cbuf);
     NED_LAUNCH_CHECK("gj_update_kernel");
     const int live = n - k0 < NB ? (n - k0 > 0 ? n - k0 : 0) : NB;
-    instr_end(slot, st, 8.0 * (double)n * n * live * nb_batch);
+    instr_end(slot, st, 8.0 * (double)n * n * live * nb_batch,
+              live > 0 ? 2.0 * sizeof(cplx_t<T>) * (double)n * n * nb_batch : 0.0);
   }
   return NEDMFT_OK;
 }

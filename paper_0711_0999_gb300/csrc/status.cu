@@ -42,7 +42,7 @@ std::atomic<bool> g_instr_on{false};
 std::atomic<bool> g_instr_timing{false};
 std::atomic<long long> g_launches{0};
 std::mutex g_instr_mu;
-struct Slot { cudaEvent_t a, b; double flops; };
+struct Slot { cudaEvent_t a, b; double flops, bytes; };
 std::vector<Slot> g_slots;
 size_t g_slot_used = 0;
 }  // namespace
@@ -64,11 +64,12 @@ int instr_begin(cudaStream_t st) {
   if (cudaEventRecord(g_slots[k].a, st) != cudaSuccess) return -1;
   return k;
 }
-void instr_end(int slot, cudaStream_t st, double flops) {
+void instr_end(int slot, cudaStream_t st, double flops, double bytes) {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_instr_mu);
   cudaEventRecord(g_slots[slot].b, st);
   g_slots[slot].flops = flops;
+  g_slots[slot].bytes = bytes;
 }
 
 int* device_status_ptr() {
@@ -131,19 +132,21 @@ extern "C" int nedmft_instrument(int enable, int timing) {
 }
 
 extern "C" int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches, double* timed_ms,
-                                      double* timed_flops) {
+                                      double* timed_flops, double* timed_bytes) {
   std::lock_guard<std::mutex> lk(g_instr_mu);
-  double ms = 0.0, fl = 0.0;
+  double ms = 0.0, fl = 0.0, by = 0.0;
   for (size_t k = 0; k < g_slot_used; ++k) {
     NED_CUDA(cudaEventSynchronize(g_slots[k].b));
     float t = 0.0f;
     NED_CUDA(cudaEventElapsedTime(&t, g_slots[k].a, g_slots[k].b));
     ms += t;
     fl += g_slots[k].flops;
+    by += g_slots[k].bytes;
   }
   if (launches) *launches = g_launches.load();
   if (timed_launches) *timed_launches = (int64_t)g_slot_used;
   if (timed_ms) *timed_ms = ms;
   if (timed_flops) *timed_flops = fl;
+  if (timed_bytes) *timed_bytes = by;
   return NEDMFT_OK;
 }

@@ -600,7 +600,7 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
       int rc = launch_gemm_persistent<CfgGJ, Split3, 8>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
       const int live = n - k0 < kNb ? (n - k0 > 0 ? n - k0 : 0) : kNb;
-      instr_end(slot, st, 8.0 * (double)n * n * live * nb);
+      instr_end(slot, st, 8.0 * (double)n * n * live * nb, live > 0 ? 2.0 * sizeof(float2) * (double)n * n * nb : 0.0);
     }
   }
   return NEDMFT_OK;
