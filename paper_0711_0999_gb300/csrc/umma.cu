@@ -367,6 +367,11 @@ struct EpiUpdate {
   float* A;
   size_t bstride;  // floats between matrices
   int np, k0;
+  // the next step's panels, written from the new values (kn < 0: last step)
+  int kn;
+  __nv_bfloat16* cimg;  // C' of step kn (the update's A operand)
+  __nv_bfloat16* timg;  // embedded A_{Kn,:}^T (the R product's B operand)
+  size_t pstride, cslice, tslice;
   // warm L2 with the tile's 128 rows of old values (1 KB each)
   __device__ void prefetch(int b, int mt, int nt) const {
     const float* base = A + b * bstride + (size_t)(mt * kTileRows) * 2 * np + nt * CfgGJ::kBn;
@@ -392,6 +397,46 @@ struct EpiUpdate {
       if (ja + 1 >= k0 && ja + 1 < k0 + kNb) { o[u].z = 0.f; o[u].w = 0.f; }
       o[u].x -= v[4 * u]; o[u].y -= v[4 * u + 1]; o[u].z -= v[4 * u + 2]; o[u].w -= v[4 * u + 3];
       *reinterpret_cast<float4*>(row + 4 * u) = o[u];
+    }
+    if (kn < 0) return;
+    if (nt * (CfgGJ::kBn / 2) == kn) {
+      // column block Kn: row i of C'_next (C'_Kn = -I)
+      __nv_bfloat16* cd = cimg + b * pstride;
+      const bool in = (i >= kn && i < kn + kNb);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = j0 + u - kn;
+        float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
+        float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
+        if (in) { re = (i - kn == c) ? -1.f : 0.f; im = 0.f; }
+        __nv_bfloat16 rh, rl, ih, il;
+        split2(re, rh, rl);
+        split2(im, ih, il);
+        const size_t off = img_offset(i, 2 * c, kKt);
+        *reinterpret_cast<__nv_bfloat162*>(cd + off) = __halves2bfloat162(rh, ih);
+        *reinterpret_cast<__nv_bfloat162*>(cd + cslice + off) = __halves2bfloat162(rl, il);
+      }
+    }
+    if (mt * kTileRows == kn) {
+      // row block Kn: row c = i - kn of A_{Kn,:}, embedded and transposed (A_{Kn,Kn} -> I)
+      __nv_bfloat16* td = timg + b * pstride;
+      const int c = i - kn;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int j = j0 + u;
+        float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
+        float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
+        if (j >= kn && j < kn + kNb) { re = (j - kn == c) ? 1.f : 0.f; im = 0.f; }
+        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        split2(re, rh, rl);
+        split2(im, ih, il);
+        split2(-im, nh, nl);
+        const size_t o0 = img_offset(2 * j, 2 * c, kKt), o1 = img_offset(2 * j + 1, 2 * c, kKt);
+        *reinterpret_cast<__nv_bfloat162*>(td + o0) = __halves2bfloat162(rh, nh);
+        *reinterpret_cast<__nv_bfloat162*>(td + o1) = __halves2bfloat162(ih, rh);
+        *reinterpret_cast<__nv_bfloat162*>(td + tslice + o0) = __halves2bfloat162(rl, nl);
+        *reinterpret_cast<__nv_bfloat162*>(td + tslice + o1) = __halves2bfloat162(il, rl);
+      }
     }
   }
 };
@@ -550,7 +595,7 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
 // ------------------------------------------------------------------ buffer layout per matrix
 
 struct GjBuffers {
-  size_t mat, pimg, cimg, timg, rimg, total;  // bytes, each 1024-aligned
+  size_t mat, pimg, cimg, timg, rimg, total;  // bytes, each 1024-aligned; cimg / timg hold two panels each
 };
 
 size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
@@ -559,9 +604,9 @@ GjBuffers gj_buffers(int np) {
   GjBuffers g{};
   g.mat = align1k(sizeof(float2) * (size_t)np * np);
   g.pimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)kNb * 2 * kNb);
-  g.cimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * kNb);
-  g.timg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * kNb);
-  g.rimg = g.timg;
+  g.cimg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * kNb);
+  g.timg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * kNb);
+  g.rimg = g.timg / 2;
   g.total = g.mat + g.pimg + g.cimg + g.timg + g.rimg;
   return g;
 }
@@ -582,20 +627,29 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
   const size_t pstride = per / 2, pslice = (size_t)kNb * 2 * kNb;
   const size_t cslice = (size_t)np * 2 * kNb;
   const size_t tslice = (size_t)2 * np * 2 * kNb;
-  for (int k0 = 0; k0 < np; k0 += kNb) {
+  // the C' / A_K^T panels alternate between two buffers: step k reads buffer
+  // k & 1 while its update writes step k+1's panels into the other one
+  const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
+  gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, 0, cimg, pstride, cslice, timg, pstride, tslice);
+  NED_LAUNCH_CHECK("gj_panel_pack_kernel");
+  for (int k0 = 0, step = 0; k0 < np; k0 += kNb, ++step) {
+    __nv_bfloat16* cur_c = cimg + (step & 1) * chalf;
+    __nv_bfloat16* cur_t = timg + (step & 1) * thalf;
+    __nv_bfloat16* nxt_c = cimg + ((step + 1) & 1) * chalf;
+    __nv_bfloat16* nxt_t = timg + ((step + 1) & 1) * thalf;
     gj_pivot_pack_kernel<<<nb, 1024, 0, st>>>(A, np, k0, pimg, pstride, pslice, status);
     NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
-    gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, k0, cimg, pstride, cslice, timg, pstride, tslice);
-    NED_LAUNCH_CHECK("gj_panel_pack_kernel");
     {  // R = P A_{K,:}, 128 x 2np, K = 256
-      GemmParams p{pimg, pstride, pslice, timg, pstride, tslice, kKt, status};
+      GemmParams p{pimg, pstride, pslice, cur_t, pstride, tslice, kKt, status};
       EpiRPack epi{rimg, pstride, tslice};
       int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, 1, nb, epi, st);
       if (rc) return rc;
     }
-    {  // A <- A - C' R, np x 2np, K = 256
-      GemmParams p{cimg, pstride, cslice, rimg, pstride, tslice, kKt, status};
-      EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0};
+    {  // A <- A - C' R, np x 2np, K = 256; next step's panels from the epilogue
+      GemmParams p{cur_c, pstride, cslice, rimg, pstride, tslice, kKt, status};
+      const int kn = (k0 + kNb < np) ? k0 + kNb : -1;
+      EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
+                    tslice};
       const int slot = instr_begin(st);
       int rc = launch_gemm_persistent<CfgGJ, Split3, 8>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
@@ -628,7 +682,7 @@ constexpr int kOzBits = 7;        // bits per slice
 constexpr int kOzPairs = 10;      // slice pairs with a + b <= kOzS - 1
 constexpr int kOzBn = 64;         // output columns per tile (32 complex)
 constexpr int kOzChunkKt = 16;    // K tiles per exact chunk (1024)
-constexpr double kRefineTail = 1e-4;
+constexpr double kRefineTail = 1e-3;
 
 __device__ __forceinline__ void oz_pair(int q, int& a, int& b, int& d) {
   // d = a + b (slice order); the accumulator of order d
