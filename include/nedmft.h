@@ -139,6 +139,13 @@ int nedmft_gauss_hermite(int32_t n, double* x_host, double* w_host);
 int nedmft_quadrature_grid(int32_t n, double* eps_host, double* ebar_host,
                            double* wq_host);
 
+/* The average of the N- and (N+1)-point product grids (Sec. II: averaging
+ * the two Gaussian quadratures works better than one 2N+1 rule): n^2 points
+ * of the n-point grid followed by (n+1)^2 points of the (n+1)-point grid,
+ * every weight halved.  Host only; arrays of n^2 + (n+1)^2.  n in [1, 511]. */
+int nedmft_quadrature_grid_avg(int32_t n, double* eps_host, double* ebar_host,
+                               double* wq_host);
+
 /* ---------------------------------------------------------------- G0 */
 
 /* Noninteracting contour Green's function of Eq. g_contour_non_final2 for
@@ -215,6 +222,20 @@ int nedmft_lattice_gloc_static(const nedmft_contour* c, const nedmft_model* m,
                                const double* ebar_d, const double* wq_d,
                                int32_t nq, nedmft_c128* gloc_d, double* j_d,
                                double* j_imag_d, void* stream);
+
+/* dt -> 0 extrapolation of the current (Sec. II, Lagrange extrapolation):
+ * out[e] = sum_r L_r(0) j_r(t_e), L_r the Lagrange basis polynomials of the
+ * k step sizes dts_host[r] (k = 3: quadratic, 4: cubic, ...), each j_r read
+ * at t_e by linear interpolation on its own upper-branch grid
+ * t_min_host[r] + m dts_host[r], m < n_t_host[r].  j_d: host array of k
+ * device pointers; t_out_d, out_d: device, n_out doubles.  Times outside a
+ * run's grid set *bad_d (device int) to 1 and leave their output unset.
+ * k in [1, 16], distinct dts.  Stream-ordered. */
+int nedmft_extrapolate_current(int32_t k, const double* dts_host,
+                               const double* t_min_host,
+                               const int32_t* n_t_host, const double* const* j_d,
+                               const double* t_out_d, int32_t n_out,
+                               double* out_d, int32_t* bad_d, void* stream);
 
 /* ---------------------------------------------------------------- impurity */
 

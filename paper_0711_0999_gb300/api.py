@@ -89,6 +89,33 @@ def quadrature_grid(n: int):
     return e, b, w
 
 
+def quadrature_grid_avg(n: int):
+    m = n * n + (n + 1) * (n + 1)
+    e, b, w = np.zeros(m), np.zeros(m), np.zeros(m)
+    N.check(N.lib().nedmft_quadrature_grid_avg(n, e.ctypes.data_as(N.PD), b.ctypes.data_as(N.PD),
+                                               w.ctypes.data_as(N.PD)))
+    return e, b, w
+
+
+def extrapolate_current(grids, currents, t_out, stream=None) -> torch.Tensor:
+    """dt -> 0 Lagrange extrapolation of j(t) from runs on several contour grids."""
+    k = len(grids)
+    dev = currents[0].device
+    dts = np.array([g.contour.dt for g in grids], dtype=np.float64)
+    tmins = np.array([g.contour.t_min for g in grids], dtype=np.float64)
+    nts = np.array([g.contour.n_t for g in grids], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * k)(*[c.data_ptr() for c in currents])
+    t_d = _dev(t_out, torch.float64, dev)
+    out = torch.empty(t_d.numel(), dtype=torch.float64, device=dev)
+    bad = torch.zeros(1, dtype=torch.int32, device=dev)
+    N.check(N.lib().nedmft_extrapolate_current(k, dts.ctypes.data_as(N.PD), tmins.ctypes.data_as(N.PD),
+                                               nts.ctypes.data_as(N.PI), ptrs, _ptr(t_d), t_d.numel(), _ptr(out),
+                                               _ptr(bad), ctypes.c_void_p(_stream(stream))))
+    if int(bad.item()):
+        raise NedmftError(N.NEDMFT_EINVAL, "extrapolate_current: an output time lies outside a run's grid")
+    return out
+
+
 def g0_build(grid: Grid, model: N.Model, eps, ebar, device="cuda", stream=None) -> torch.Tensor:
     eps_t = _dev(eps, torch.float64, device)
     ebar_t = _dev(ebar, torch.float64, device)

@@ -212,3 +212,21 @@ def test_dmft_solve_small_config_matches_oracle():
     w = c.w
     sw = lambda s: w[:, None] * s * w[None, :]
     assert rel(sw(sol.sigma.cpu().numpy()), sw(ref.sigma)) < 1e-8
+
+
+def test_long_contour_sampled_points():
+    # N_c = 3400 contour (t in [-5, 50], dt = 1/30, dtau = 0.1), U = 2, E = 1:
+    # the Mott-insulating long-time shape; 8 points of the 64 x 64 grid near its
+    # centre, with their own weights renormalised (an integral-like sample)
+    args = (-5, 50, 1 / 30, 10.0, 0.1)
+    c, g, mo, mc, sig, _, _, _ = setup(args, 2.0, 1.0, 2, seed=21)
+    assert c.n_c == 3400
+    eps_all, ebar_all, wq_all = O.quadrature_points(64)
+    pick = [a * 64 + b for a in (30, 33) for b in (27, 31, 33, 37)]
+    eps, ebar, wq = eps_all[pick], ebar_all[pick], wq_all[pick] / wq_all[pick].sum()
+    ref, jref = O.lattice_gloc(c, mo, sig, eps, ebar, wq)
+    for prec in ("mixed_bf16", "fp64"):
+        gl, j, _ = run_gpu(g, mc, sig, eps, ebar, wq, prec)
+        tg, tj = TOL[prec]
+        assert rel(gl, ref) < tg, prec
+        assert np.abs(j - jref.real).max() < tj, prec

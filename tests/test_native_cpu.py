@@ -95,3 +95,16 @@ def test_status_strings():
     for code in (0, -1, -2, -3, -4, -5, 1):
         assert lib.nedmft_status_string(code)
     assert lib.nedmft_status_string(-99) == b"unknown status"
+
+
+def test_quadrature_grid_avg_matches_oracle():
+    e, b, w = api.quadrature_grid_avg(6)
+    e6, b6, w6 = O.quadrature_points(6)
+    e7, b7, w7 = O.quadrature_points(7)
+    assert len(e) == 36 + 49
+    assert np.abs(e - np.concatenate([e6, e7])).max() < 1e-13
+    assert np.abs(b - np.concatenate([b6, b7])).max() < 1e-13
+    assert np.abs(w - 0.5 * np.concatenate([w6, w7])).max() < 1e-15
+    assert abs(w.sum() - 1.0) < 1e-14
+    with pytest.raises(N.NedmftError):
+        api.quadrature_grid_avg(0)
