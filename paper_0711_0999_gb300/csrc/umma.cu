@@ -317,15 +317,30 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel
       const int buf = lt & 1;
       if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) break;
       tc_fence_after();
+      const int md = epi.mode(mt, nt);
 #pragma unroll 1
       for (int c0 = part * kSpan; c0 < (part + 1) * kSpan; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
-        epi(b, mt, nt, row, c0, v);
+        if (Epi::kStage && md == 0) {
+          // -acc through a private 144-byte staging row, added into the
+          // output row at L2 by one bulk reduction (no load on the SM)
+          float* srow = reinterpret_cast<float*>(smem + C::kStages * C::kStageBytes + 256) + ((warp - 2) * 32 + lane) * 36;
+          bulk_wait_read();
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            reinterpret_cast<float4*>(srow)[u] = make_float4(-v[4 * u], -v[4 * u + 1], -v[4 * u + 2], -v[4 * u + 3]);
+          fence_proxy_async();
+          bulk_reduce_add_f32(epi.row_ptr(b, mt, nt, row) + c0, srow, 128);
+          bulk_commit();
+        } else {
+          epi(b, mt, nt, row, c0, v);
+        }
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
     }
+    if (Epi::kStage) bulk_wait_all();
   }
   __syncthreads();
   if (warp == 1) {
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel
 
 template <class C, class Pairs, int EPIW, class Epi>
 int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
-  const int smem_bytes = C::kSmem;
+  const int smem_bytes = C::kSmem + (Epi::kStage ? EPIW * 32 * 144 : 0);
   static bool attr = false;
   if (!attr) {
     NED_CUDA(cudaFuncSetAttribute(umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>,
@@ -364,6 +379,7 @@ int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int ba
 
 // A <- A(rows K and columns K zeroed) - acc, A interleaved FP32 (row stride 2 np floats).
 struct EpiUpdate {
+  static constexpr bool kStage = true;
   float* A;
   size_t bstride;  // floats between matrices
   int np, k0;
@@ -372,8 +388,20 @@ struct EpiUpdate {
   __nv_bfloat16* cimg;  // C' of step kn (the update's A operand)
   __nv_bfloat16* timg;  // embedded A_{Kn,:}^T (the R product's B operand)
   size_t pstride, cslice, tslice;
+  // 0: plain tile, A += -acc by bulk reduction at L2; 1: rows or columns of
+  // block K (new value = -acc); 2: the next step's panel blocks (new values
+  // needed in registers)
+  __device__ int mode(int mt, int nt) const {
+    if (kn >= 0 && (nt * (CfgGJ::kBn / 2) == kn || mt * kTileRows == kn)) return 2;
+    if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return 1;
+    return 0;
+  }
+  __device__ float* row_ptr(int b, int mt, int nt, int r) const {
+    return A + b * bstride + (size_t)(mt * kTileRows + r) * 2 * np + nt * CfgGJ::kBn;
+  }
   // warm L2 with the tile's 128 rows of old values (1 KB each)
   __device__ void prefetch(int b, int mt, int nt) const {
+    if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return;  // old values unused
     const float* base = A + b * bstride + (size_t)(mt * kTileRows) * 2 * np + nt * CfgGJ::kBn;
     for (int r = 0; r < kTileRows; ++r)
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + (size_t)r * 2 * np),
@@ -386,10 +414,11 @@ struct EpiUpdate {
     float* row = A + b * bstride + (size_t)i * 2 * np + n0;
     const bool ik = (i >= k0 && i < k0 + kNb);
     const int j0 = n0 >> 1;  // first complex column of the chunk
+    const bool skip = ik || (nt * (CfgGJ::kBn / 2) == k0);  // the whole chunk lies in block K
     float4 o[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      o[u] = ik ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
+      o[u] = skip ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int ja = j0 + 2 * u;
@@ -444,6 +473,9 @@ struct EpiUpdate {
 // R (kNb x np complex, acc rows = R rows) -> the update's B operand image:
 // rows n = 2j, 2j+1; k = 2r, 2r+1 with [[re, -im], [im, re]].
 struct EpiRPack {
+  static constexpr bool kStage = false;
+  __device__ int mode(int, int) const { return 1; }
+  __device__ float* row_ptr(int, int, int, int) const { return nullptr; }
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 kNb)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
@@ -651,7 +683,7 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
       EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
                     tslice};
       const int slot = instr_begin(st);
-      int rc = launch_gemm_persistent<CfgGJ, Split3, 8>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
+      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
       const int live = n - k0 < kNb ? (n - k0 > 0 ? n - k0 : 0) : kNb;
       instr_end(slot, st, 8.0 * (double)n * n * live * nb, live > 0 ? 2.0 * sizeof(float2) * (double)n * n * nb : 0.0);
