@@ -78,6 +78,18 @@ SIGNATURES = {
     "nedmft_impurity_workspace_size": (c_size_t, [PC]),
     "nedmft_impurity_update": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                               c_void_p]),
+    "nedmft_mlp_param_count": (c_int32, []),
+    "nedmft_mlp_workspace_size": (c_size_t, [c_int32]),
+    "nedmft_mlp_forward": (ctypes.c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nedmft_mlp_grad": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t,
+                                       c_void_p]),
+    "nedmft_mlp_adam": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float, c_void_p]),
+    "nedmft_mlp_features": (ctypes.c_int, [PC, PM, c_void_p, c_void_p]),
+    "nedmft_mlp_target": (ctypes.c_int, [PC, PM, c_void_p, c_double, c_void_p, c_void_p]),
+    "nedmft_mlp_sample": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int64, c_int32, ctypes.c_uint64, ctypes.c_int64,
+                                         c_void_p, c_void_p, c_void_p]),
+    "nedmft_sigma_warm_start_workspace_size": (c_size_t, [PC]),
+    "nedmft_sigma_warm_start": (ctypes.c_int, [PC, PM, c_void_p, c_double, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nedmft_dmft_workspace_size": (c_size_t, [PC, c_int32, ctypes.c_int]),
     "nedmft_dmft_solve": (ctypes.c_int, [PC, PM, c_int32, ctypes.c_int, c_void_p, c_double, c_int32, c_void_p,
                                          c_void_p, c_void_p, PI, PD, c_void_p, c_size_t, c_void_p]),

@@ -1,0 +1,415 @@
+// Learned warm start of the self-energy: a small MLP maps (U, E, t, t') to
+// the smooth part of Sigma(t, t'); the point-split band U<w_1> delta_c is
+// added in closed form.  Forward, backward (mean-squared error) and Adam are
+// hand-written kernels; GEMM operands are rounded to bf16 and accumulated in
+// FP32, weights and optimizer state are FP32.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nedmft {
+namespace {
+
+constexpr int kIn = 14;      // features per (t, t') pair
+constexpr int kHid = 256;    // width of the four hidden layers
+constexpr int kOut = 2;      // Re, Im of the smooth Sigma part
+constexpr int kLayers = 5;   // 4 hidden + output
+constexpr int kDims[kLayers + 1] = {kIn, kHid, kHid, kHid, kHid, kOut};
+
+constexpr size_t w_off(int l) {  // host only: offsets are passed to kernels as pointers
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)kDims[i] * kDims[i + 1] + kDims[i + 1];
+  return o;
+}
+constexpr size_t kParams = w_off(kLayers);
+
+__device__ __forceinline__ float bf16r(float x) {  // round to the nearest bf16 value
+  uint32_t u = __float_as_uint(x);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return __uint_as_float(u & 0xffff0000u);
+}
+
+// C[m x n] = op(A) op(B) (+ bias[n]) with A m x k (ta: A stored k x m) and
+// B k x n (tb: B stored n x k), FP32 in memory, bf16-rounded operands, FP32
+// accumulation.  64 x 64 tiles, 256 threads.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) mlp_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                                       const float* __restrict__ bias, float* __restrict__ C, int m,
+                                                       int n, int k, bool accumulate) {
+  __shared__ float as[16][65], bs[16][65];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e / 64, ii = e % 64;
+      const int gi = i0 + ii, gk = k0 + kk;
+      float va = 0.f;
+      if (gi < m && gk < k) va = TA ? A[(size_t)gk * m + gi] : A[(size_t)gi * k + gk];
+      as[kk][ii] = bf16r(va);
+      const int gj = j0 + ii;
+      float vb = 0.f;
+      if (gj < n && gk < k) vb = TB ? B[(size_t)gj * k + gk] : B[(size_t)gk * n + gj];
+      bs[kk][ii] = bf16r(vb);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = as[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], b[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * q;
+      if (gi < m && gj < n) {
+        float v = acc[r][q] + (bias ? bias[gj] : 0.f);
+        if (accumulate) v += C[(size_t)gi * n + gj];
+        C[(size_t)gi * n + gj] = v;
+      }
+    }
+}
+
+template <bool TA, bool TB>
+int gemm(const float* A, const float* B, const float* bias, float* C, int m, int n, int k, bool acc, cudaStream_t st) {
+  mlp_gemm_kernel<TA, TB><<<dim3(ceil_div(n, 64), ceil_div(m, 64)), 256, 0, st>>>(A, B, bias, C, m, n, k, acc);
+  NED_LAUNCH_CHECK("mlp_gemm_kernel");
+  return NEDMFT_OK;
+}
+
+__global__ void tanh_kernel(float* __restrict__ h, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    h[e] = tanhf(h[e]);
+}
+
+// dZ = dH * (1 - H^2) in place on dH (H = tanh(Z))
+__global__ void tanh_back_kernel(const float* __restrict__ h, float* __restrict__ d, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    d[e] *= 1.f - h[e] * h[e];
+}
+
+// dY = 2 (Y - T) / n, loss partial sums per block
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dy, size_t n,
+                           float inv, double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float r = y[e] - t[e];
+    dy[e] = 2.f * r * inv;
+    s += (double)r * r;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_finish_kernel(const double* __restrict__ part, int nb, double inv, float* __restrict__ loss) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int i = 0; i < nb; ++i) s += part[i];
+  *loss = (float)(s * inv);
+}
+
+// db[j] = sum_i d[i][j]
+__global__ void bias_grad_kernel(const float* __restrict__ d, int m, int n, float* __restrict__ db) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float s = 0.f;
+  for (int i = 0; i < m; ++i) s += d[(size_t)i * n + j];
+  db[j] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float gg = g[e];
+    const float a = b1 * m1[e] + (1.f - b1) * gg;
+    const float b = b2 * m2[e] + (1.f - b2) * gg * gg;
+    m1[e] = a;
+    m2[e] = b;
+    p[e] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+  }
+}
+
+// Features of the pair (t_i, t_j): U/2.5, E/4, Re(t_i - t_j)/20,
+// (tau_i - tau_j)/beta, then for each time Re t / 20, tau / beta and the
+// branch one-hot (upper, lower, imaginary).
+__global__ void features_kernel(ContourDev c, ModelDev m, float* __restrict__ x) {
+  const size_t total = (size_t)c.n * c.n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / c.n), j = (int)(e % c.n);
+    float* f = x + e * kIn;
+    f[0] = (float)(m.U / 2.5);
+    f[1] = (float)(m.E / 4.0);
+    f[2] = (float)((t_re(c, i) - t_re(c, j)) / 20.0);
+    f[3] = (float)((t_tau(c, i) - t_tau(c, j)) / c.beta);
+    const int ij[2] = {i, j};
+    for (int s = 0; s < 2; ++s) {
+      const int k = ij[s];
+      f[4 + 5 * s] = (float)(t_re(c, k) / 20.0);
+      f[5 + 5 * s] = (float)(t_tau(c, k) / c.beta);
+      f[6 + 5 * s] = k < c.nt ? 1.f : 0.f;
+      f[7 + 5 * s] = (k >= c.nt && k < 2 * c.nt) ? 1.f : 0.f;
+      f[8 + 5 * s] = k >= 2 * c.nt ? 1.f : 0.f;
+    }
+  }
+}
+
+// Sigma = band + scale * y: the point-split band (U w1) delta_c
+// (Sigma_{j,j-1} = U w1 / W_{j-1}, boundary element -U w1 / W_{N-1}) plus the
+// network's smooth part.
+__global__ void assemble_sigma_kernel(ContourDev c, ModelDev m, const float* __restrict__ y, double scale,
+                                      double2* __restrict__ sigma) {
+  const size_t total = (size_t)c.n * c.n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / c.n), j = (int)(e % c.n);
+    double2 v = make_double2(scale * y[2 * e], scale * y[2 * e + 1]);
+    const double h = m.U * m.w1;
+    if (j == i - 1) {
+      const double2 w = weight(c, j);
+      const double d = w.x * w.x + w.y * w.y;
+      v.x += h * w.x / d;
+      v.y -= h * w.y / d;
+    }
+    if (i == 0 && j == c.n - 1) {
+      const double2 w = weight(c, c.n - 1);
+      const double d = w.x * w.x + w.y * w.y;
+      v.x -= h * w.x / d;
+      v.y += h * w.y / d;
+    }
+    sigma[e] = v;
+  }
+}
+
+// The training target: the smooth part (Sigma minus the band) / scale.
+__global__ void target_kernel(ContourDev c, ModelDev m, const double2* __restrict__ sigma, double inv_scale,
+                              float* __restrict__ t) {
+  const size_t total = (size_t)c.n * c.n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / c.n), j = (int)(e % c.n);
+    double2 v = sigma[e];
+    const double h = m.U * m.w1;
+    if (j == i - 1) {
+      const double2 w = weight(c, j);
+      const double d = w.x * w.x + w.y * w.y;
+      v.x -= h * w.x / d;
+      v.y += h * w.y / d;
+    }
+    if (i == 0 && j == c.n - 1) {
+      const double2 w = weight(c, c.n - 1);
+      const double d = w.x * w.x + w.y * w.y;
+      v.x += h * w.x / d;
+      v.y -= h * w.y / d;
+    }
+    t[2 * e] = (float)(v.x * inv_scale);
+    t[2 * e + 1] = (float)(v.y * inv_scale);
+  }
+}
+
+int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+// activations for n samples: 4 hidden layers + output
+size_t act_floats(int n) { return (size_t)n * (4 * kHid + kOut); }
+
+}  // namespace
+}  // namespace nedmft
+
+using namespace nedmft;
+
+extern "C" int32_t nedmft_mlp_param_count(void) { return (int32_t)kParams; }
+
+extern "C" size_t nedmft_mlp_workspace_size(int32_t n) {
+  if (n < 1) return 0;
+  // activations + their gradients (2 x act) + loss partials
+  return align256(sizeof(float) * act_floats(n)) * 2 + align256(sizeof(double) * 152 * 16);
+}
+
+extern "C" int nedmft_mlp_forward(const float* params_d, const float* x_d, int32_t n, float* y_d, void* ws_d,
+                                  size_t ws_bytes, void* stream) {
+  if (!params_d || !x_d || !y_d || !ws_d || n < 1) return set_error(NEDMFT_EINVAL, "mlp_forward: bad argument");
+  if (ws_bytes < nedmft_mlp_workspace_size(n)) return set_error(NEDMFT_ENOMEM, "mlp_forward: workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* act = static_cast<float*>(ws_d);
+  const float* in = x_d;
+  for (int l = 0; l < kLayers; ++l) {
+    const float* W = params_d + w_off(l);  // kDims[l] x kDims[l+1], row-major
+    const float* b = W + (size_t)kDims[l] * kDims[l + 1];
+    float* out = (l == kLayers - 1) ? y_d : act + (size_t)n * kHid * l;
+    int rc = gemm<false, false>(in, W, b, out, n, kDims[l + 1], kDims[l], false, st);
+    if (rc) return rc;
+    if (l < kLayers - 1) {
+      tanh_kernel<<<grid_for((size_t)n * kHid), 256, 0, st>>>(out, (size_t)n * kHid);
+      NED_LAUNCH_CHECK("tanh_kernel");
+    }
+    in = out;
+  }
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_mlp_grad(const float* params_d, const float* x_d, const float* target_d, int32_t n,
+                               float* grad_d, float* loss_d, void* ws_d, size_t ws_bytes, void* stream) {
+  if (!params_d || !x_d || !target_d || !grad_d || !loss_d || !ws_d || n < 1)
+    return set_error(NEDMFT_EINVAL, "mlp_grad: bad argument");
+  if (ws_bytes < nedmft_mlp_workspace_size(n)) return set_error(NEDMFT_ENOMEM, "mlp_grad: workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* p = static_cast<char*>(ws_d);
+  float* act = reinterpret_cast<float*>(p);
+  float* dact = reinterpret_cast<float*>(p + align256(sizeof(float) * act_floats(n)));
+  double* part = reinterpret_cast<double*>(p + 2 * align256(sizeof(float) * act_floats(n)));
+  float* H[kLayers];
+  float* D[kLayers];
+  for (int l = 0; l < kLayers; ++l) {
+    H[l] = act + (size_t)n * kHid * l;
+    D[l] = dact + (size_t)n * kHid * l;
+  }
+  // forward, keeping every activation (H[4] = output)
+  const float* in = x_d;
+  for (int l = 0; l < kLayers; ++l) {
+    const float* W = params_d + w_off(l);
+    const float* b = W + (size_t)kDims[l] * kDims[l + 1];
+    int rc = gemm<false, false>(in, W, b, H[l], n, kDims[l + 1], kDims[l], false, st);
+    if (rc) return rc;
+    if (l < kLayers - 1) {
+      tanh_kernel<<<grid_for((size_t)n * kHid), 256, 0, st>>>(H[l], (size_t)n * kHid);
+      NED_LAUNCH_CHECK("tanh_kernel");
+    }
+    in = H[l];
+  }
+  const size_t no = (size_t)n * kOut;
+  const int nbl = grid_for(no);
+  mse_kernel<<<nbl, 256, 0, st>>>(H[kLayers - 1], target_d, D[kLayers - 1], no, 1.f / (float)no, part);
+  NED_LAUNCH_CHECK("mse_kernel");
+  loss_finish_kernel<<<1, 32, 0, st>>>(part, nbl, 1.0 / (double)no, loss_d);
+  NED_LAUNCH_CHECK("loss_finish_kernel");
+  for (int l = kLayers - 1; l >= 0; --l) {
+    const float* W = params_d + w_off(l);
+    float* gW = grad_d + w_off(l);
+    float* gb = gW + (size_t)kDims[l] * kDims[l + 1];
+    const float* xin = l == 0 ? x_d : H[l - 1];
+    // dW = xin^T D[l], db = column sums of D[l]
+    int rc = gemm<true, false>(xin, D[l], nullptr, gW, kDims[l], kDims[l + 1], n, false, st);
+    if (rc) return rc;
+    bias_grad_kernel<<<ceil_div(kDims[l + 1], 128), 128, 0, st>>>(D[l], n, kDims[l + 1], gb);
+    NED_LAUNCH_CHECK("bias_grad_kernel");
+    if (l > 0) {
+      // D[l-1] = (D[l] W^T) * tanh'(.)
+      rc = gemm<false, true>(D[l], W, nullptr, D[l - 1], n, kDims[l], kDims[l + 1], false, st);
+      if (rc) return rc;
+      tanh_back_kernel<<<grid_for((size_t)n * kHid), 256, 0, st>>>(H[l - 1], D[l - 1], (size_t)n * kHid);
+      NED_LAUNCH_CHECK("tanh_back_kernel");
+    }
+  }
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_mlp_adam(float* params_d, const float* grad_d, float* m1_d, float* m2_d, int32_t step, float lr,
+                               void* stream) {
+  if (!params_d || !grad_d || !m1_d || !m2_d || step < 1) return set_error(NEDMFT_EINVAL, "mlp_adam: bad argument");
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  adam_kernel<<<grid_for(kParams), 256, 0, static_cast<cudaStream_t>(stream)>>>(params_d, grad_d, m1_d, m2_d, kParams,
+                                                                                 lr, b1, b2, 1e-8f, c1, c2);
+  NED_LAUNCH_CHECK("adam_kernel");
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_mlp_features(const nedmft_contour* c, const nedmft_model* m, float* x_d, void* stream) {
+  if (!c || !m || !x_d || c->n_c < 1) return set_error(NEDMFT_EINVAL, "mlp_features: bad argument");
+  const ContourDev cd = to_dev(*c);
+  const ModelDev md{m->U, m->E, m->w1, isnan(m->mu) ? m->U / 2 : m->mu};
+  features_kernel<<<grid_for((size_t)cd.n * cd.n), 256, 0, static_cast<cudaStream_t>(stream)>>>(cd, md, x_d);
+  NED_LAUNCH_CHECK("features_kernel");
+  return NEDMFT_OK;
+}
+
+extern "C" int nedmft_mlp_target(const nedmft_contour* c, const nedmft_model* m, const nedmft_c128* sigma_d,
+                                 double scale, float* t_d, void* stream) {
+  if (!c || !m || !sigma_d || !t_d || !(scale > 0)) return set_error(NEDMFT_EINVAL, "mlp_target: bad argument");
+  const ContourDev cd = to_dev(*c);
+  const ModelDev md{m->U, m->E, m->w1, isnan(m->mu) ? m->U / 2 : m->mu};
+  target_kernel<<<grid_for((size_t)cd.n * cd.n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      cd, md, reinterpret_cast<const double2*>(sigma_d), 1.0 / scale, t_d);
+  NED_LAUNCH_CHECK("target_kernel");
+  return NEDMFT_OK;
+}
+
+extern "C" size_t nedmft_sigma_warm_start_workspace_size(const nedmft_contour* c) {
+  if (!c || c->n_c < 1) return 0;
+  const size_t n2 = (size_t)c->n_c * c->n_c;
+  return align256(sizeof(float) * n2 * kIn) + align256(sizeof(float) * n2 * kOut) +
+         nedmft_mlp_workspace_size((int32_t)(n2 > 65536 ? 65536 : n2));
+}
+
+extern "C" int nedmft_sigma_warm_start(const nedmft_contour* c, const nedmft_model* m, const float* params_d,
+                                       double scale, nedmft_c128* sigma_d, void* ws_d, size_t ws_bytes, void* stream) {
+  if (!c || !m || !params_d || !sigma_d || !ws_d || !(scale > 0))
+    return set_error(NEDMFT_EINVAL, "sigma_warm_start: bad argument");
+  if (ws_bytes < nedmft_sigma_warm_start_workspace_size(c))
+    return set_error(NEDMFT_ENOMEM, "sigma_warm_start: workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n2 = (size_t)c->n_c * c->n_c;
+  char* p = static_cast<char*>(ws_d);
+  float* x = reinterpret_cast<float*>(p);
+  float* y = reinterpret_cast<float*>(p + align256(sizeof(float) * n2 * kIn));
+  char* mws = p + align256(sizeof(float) * n2 * kIn) + align256(sizeof(float) * n2 * kOut);
+  int rc = nedmft_mlp_features(c, m, x, stream);
+  if (rc) return rc;
+  for (size_t s = 0; s < n2; s += 65536) {  // evaluate in chunks of 65536 pairs
+    const int cnt = (int)((n2 - s) < 65536 ? (n2 - s) : 65536);
+    rc = nedmft_mlp_forward(params_d, x + s * kIn, cnt, y + s * kOut, mws, nedmft_mlp_workspace_size(cnt), stream);
+    if (rc) return rc;
+  }
+  const ContourDev cd = to_dev(*c);
+  const ModelDev md{m->U, m->E, m->w1, isnan(m->mu) ? m->U / 2 : m->mu};
+  assemble_sigma_kernel<<<grid_for(n2), 256, 0, st>>>(cd, md, y, scale, reinterpret_cast<double2*>(sigma_d));
+  NED_LAUNCH_CHECK("assemble_sigma_kernel");
+  return NEDMFT_OK;
+}
+
+namespace nedmft {
+namespace {
+// x_b[r] = x[idx(r)], t_b[r] = t[idx(r)], idx from a counter-based hash of
+// (seed, step, r) (splitmix64 finaliser) modulo n_total.
+__global__ void sample_kernel(const float* __restrict__ x, const float* __restrict__ t, long long n_total, int batch,
+                              unsigned long long seed, long long step, float* __restrict__ xb, float* __restrict__ tb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= batch) return;
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(step * (long long)batch + r + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const long long i = (long long)(z % (unsigned long long)n_total);
+  for (int f = 0; f < kIn; ++f) xb[(size_t)r * kIn + f] = x[(size_t)i * kIn + f];
+  for (int f = 0; f < kOut; ++f) tb[(size_t)r * kOut + f] = t[(size_t)i * kOut + f];
+}
+}  // namespace
+}  // namespace nedmft
+
+extern "C" int nedmft_mlp_sample(const float* x_d, const float* t_d, int64_t n_total, int32_t batch, uint64_t seed,
+                                 int64_t step, float* xb_d, float* tb_d, void* stream) {
+  if (!x_d || !t_d || !xb_d || !tb_d || n_total < 1 || batch < 1)
+    return set_error(NEDMFT_EINVAL, "mlp_sample: bad argument");
+  sample_kernel<<<ceil_div(batch, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x_d, t_d, n_total, batch, seed,
+                                                                                      step, xb_d, tb_d);
+  NED_LAUNCH_CHECK("sample_kernel");
+  return NEDMFT_OK;
+}
