@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = 2 x cores)")
     ap.add_argument("--n-quad", type=int, default=0, help="override the quadrature size (profiling runs only)")
+    ap.add_argument("--tts", action="store_true",
+                    help="time to a converged solution: mixed + learned warm start vs mixed zero start vs FP64")
+    ap.add_argument("--tts-train-runs", type=int, default=64)
+    ap.add_argument("--tts-eval", type=int, default=4)
     return ap.parse_args()
 
 
@@ -204,6 +208,77 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ time to solution
+
+
+def run_tts(args):
+    """Converged DMFT at N_c = 1500 (tol 1e-6, the paper's pointwise criterion):
+    mixed path from Sigma = 0, mixed path from the learned warm start, and the FP64
+    path (one lattice step + one impurity step measured, times the iterations of
+    the converged mixed run).  The network is trained on runs shaped like the
+    warm-start configuration: U ~ U[0.25, 2.5], E ~ U[0.25, 4] (seed 20071101),
+    N_c = 400 (t in [-5, 10], dt = 0.1, dtau = 0.1), 32 x 32 points."""
+    import torch
+
+    from paper_0711_0999_gb300 import api, warmstart
+
+    torch.cuda.set_device(0)
+    W = WORKLOAD
+    tol = 1e-6
+    rng = np.random.default_rng(20071101)
+    train = list(zip(rng.uniform(0.25, 2.5, args.tts_train_runs), rng.uniform(0.25, 4.0, args.tts_train_runs)))
+    rng2 = np.random.default_rng(20071102)
+    held = list(zip(rng2.uniform(0.25, 2.5, args.tts_eval), rng2.uniform(0.25, 4.0, args.tts_eval)))
+    t0 = time.perf_counter()
+    x, t, its = warmstart.collect(train, (-5.0, 10.0, 0.1, 10.0, 0.1), 32, "mixed_bf16", tol=1e-7, max_iter=150)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, losses = warmstart.train(x, t, steps=6000, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    g = api.contour_grid(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"])
+    rows = []
+    for U, E in held:
+        m = api.make_model(float(U), float(E))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        zero = api.dmft_solve(g, m, W["n_quad"], "mixed_bf16", tol=tol, max_iter=150)
+        t_zero = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        s0 = warmstart.warm_start(g, m, params)
+        warm = api.dmft_solve(g, m, W["n_quad"], "mixed_bf16", sigma_init=s0, tol=tol, max_iter=150)
+        t_warm = time.perf_counter() - t0
+        diff = float((warm.gloc - zero.gloc).abs().max() / zero.gloc.abs().max())
+        rows.append({"U": float(U), "E": float(E), "iters_zero": zero.iterations, "iters_warm": warm.iterations,
+                     "s_zero": t_zero, "s_warm": t_warm, "gloc_rel_diff": diff,
+                     "converged": bool(zero.converged and warm.converged)})
+    # FP64: one lattice step and one impurity step, timed
+    m = api.make_model(float(held[0][0]), float(held[0][1]))
+    eps, ebar, wq = api.quadrature_grid(W["n_quad"])
+    sig = torch.zeros((g.n_c, g.n_c), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gl, _, _ = api.lattice_gloc(g, m, sig, eps, ebar, wq, precision="fp64")
+    torch.cuda.synchronize()
+    t_lat64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    api.impurity_update(g, m, gl, sig)
+    torch.cuda.synchronize()
+    t_imp = time.perf_counter() - t0
+    it_zero = np.mean([r["iters_zero"] for r in rows])
+    line = {"experiment": "time_to_solution", "tol": tol, "config": W["name"],
+            "train": {"runs": len(train), "n_c": 400, "points": 1024, "collect_s": t_collect, "train_s": t_train,
+                      "loss_start": float(losses[:20].mean()), "loss_end": float(losses[-100:].mean()),
+                      "iters_per_run": its},
+            "runs": rows,
+            "mixed_zero_s": float(np.mean([r["s_zero"] for r in rows])),
+            "mixed_warm_s": float(np.mean([r["s_warm"] for r in rows])),
+            "fp64_iteration_s": t_lat64 + t_imp, "fp64_impurity_s": t_imp,
+            "fp64_s_estimated": (t_lat64 + t_imp) * it_zero,
+            "note": "fp64_s_estimated = measured FP64 lattice + impurity step x mean zero-start iterations"}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 
@@ -214,6 +289,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.tts:
+        run_tts(args)
         return
 
     import torch
@@ -343,6 +421,16 @@ def main():
         e2e = {"value": world * args.steps / e_s, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # one impurity step on the same stream (not part of the timed lattice step)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ws_imp = api.workspace(N.lib().nedmft_impurity_workspace_size(N.ctypes.byref(grid.contour)), dev)
+    ev2.record(stream)
+    api.impurity_update(grid, model, gloc, sigma, ws=ws_imp, stream=stream)
+    ev3.record(stream)
+    torch.cuda.synchronize(dev)
+    imp_ms = ev2.elapsed_time(ev3)
+
     peaks, src = load_peaks()
     roof = roofline_for(prec, kern_tflops, kern_gbs, peaks, src, clk)
     roof["kernel"] = "Gauss-Jordan trailing update"
@@ -359,6 +447,7 @@ def main():
                            "l2": "inputs larger than L2 (every step streams >1 GB)"},
                 "tflops": tflops_step, "tflops_basis": "B-form 8 N_c^3 per solve",
                 "solves_per_s": value * nq,
+                "impurity_ms": imp_ms, "dmft_iteration_ms": ms_per_step + imp_ms,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches.value),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
