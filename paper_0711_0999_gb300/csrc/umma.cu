@@ -203,9 +203,18 @@ using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (
 // the TMEM holds two accumulators, so the epilogue of one tile overlaps the
 // loads and products of the next.  Epi::prefetch(b, mt, nt) may warm L2 for
 // the epilogue's own reads.
+// Epilogues with Epi::kStage stage -acc of plain tiles in shared memory, one
+// 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, kRedBuf
+// boxes per warp, and add it into the output at L2 with one tensor bulk
+// reduction per box through Epi::red_map.
+constexpr int kRedBuf = 2;
+constexpr int kRedBox = 32 * 32 * 4;
+template <int EPIW>
+constexpr int red_stage_bytes() { return 768 + EPIW * kRedBuf * kRedBox; }
+
 template <class C, class Pairs, class Epi, int EPIW>
-__global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel(GemmParams p, Epi epi, int n_tiles,
-                                                                                 int m_tiles, int batch) {
+__global__ void __launch_bounds__(64 + 32 * EPIW, 1)
+    umma_gemm_persistent_kernel(GemmParams p, const __grid_constant__ Epi epi, int n_tiles, int m_tiles, int batch) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
@@ -227,6 +236,10 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
       mbar_init(&acc_empty[s], 32 * EPIW);
+    }
+    if (Epi::kStage) {
+      uint64_t* box_bar = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + 128);
+      for (int k = 0; k < EPIW * kRedBuf; ++k) mbar_init(&box_bar[k], 1);
     }
     *abort_flag = 0;
     fence_barrier_init();
@@ -309,36 +322,100 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel
     const int part = (warp - 2) >> 2;
     constexpr int kParts = EPIW / 4;
     constexpr int kSpan = C::kBn / kParts;
-    const int row = q * 32 + lane;
+    // staging boxes start 1 KB after the barrier block (1024-byte aligned for
+    // the swizzle); box k of this warp has the load barrier box_bar[k]
+    unsigned char* red_stage = smem + C::kStages * C::kStageBytes + 1024 + (warp - 2) * kRedBuf * kRedBox;
+    uint64_t* box_bar = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + 128) + (warp - 2) * kRedBuf;
+    uint32_t box_phase = 0;    // bit k: parity of box_bar[k]'s next completion
+    uint32_t box_loading = 0;  // bit k: a load into box k is in flight
+    int nred = 0;
     int lt = 0;
-    for (int t = blockIdx.x; t < total; t += G, ++lt) {
+    bool ok = true;
+    for (int t = blockIdx.x; t < total && ok; t += G, ++lt) {
       const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
       const int mt = rem / n_tiles, nt = rem % n_tiles;
       const int buf = lt & 1;
-      if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) break;
-      tc_fence_after();
       const int md = epi.mode(mt, nt);
+      const int row = q * 32 + lane;
+      const int c_begin = part * kSpan, c_end = (part + 1) * kSpan;
+      // mode 2 tiles need the old values on the SM: chunk c's 32 x 32 box is
+      // loaded into box (c & 1) one chunk ahead, the first before the wait
+      auto load_box = [&](int k, int c0) {
+        if constexpr (Epi::kStage) {
+          if (lane == 0) {
+            bulk_wait_read();  // no bulk operation still reads a box of this warp
+            mbar_arrive_expect_tx(&box_bar[k], kRedBox);
+            tma_load_2d(&epi.red_map, red_stage + k * kRedBox, epi.red_x(nt, c0), epi.red_y(b, mt, q * 32),
+                        &box_bar[k]);
+          }
+          box_loading |= 1u << k;
+        }
+      };
+      if constexpr (Epi::kStage) {
+        if (md == 2) load_box(0, c_begin);
+      }
+      // waits are made warp-uniform: the loop below issues .sync.aligned loads
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag))) break;
+      tc_fence_after();
 #pragma unroll 1
-      for (int c0 = part * kSpan; c0 < (part + 1) * kSpan; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
-        if (Epi::kStage && md == 0) {
-          // -acc through a private 144-byte staging row, added into the
-          // output row at L2 by one bulk reduction (no load on the SM)
-          float* srow = reinterpret_cast<float*>(smem + C::kStages * C::kStageBytes + 256) + ((warp - 2) * 32 + lane) * 36;
-          bulk_wait_read();
+        if constexpr (Epi::kStage) {
+          const int k = md == 2 ? ((c0 - c_begin) >> 5) & 1 : nred % kRedBuf;
+          unsigned char* box = red_stage + k * kRedBox;
+          if (md == 2) {
+            if (c0 + 32 < c_end) load_box(k ^ 1, c0 + 32);
+            if (!__all_sync(0xffffffffu, mbar_wait(&box_bar[k], (box_phase >> k) & 1, abort_flag))) {
+              ok = false;
+              break;
+            }
+            box_phase ^= 1u << k;
+            box_loading &= ~(1u << k);
+            float4 o[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
-            reinterpret_cast<float4*>(srow)[u] = make_float4(-v[4 * u], -v[4 * u + 1], -v[4 * u + 2], -v[4 * u + 3]);
+            for (int u = 0; u < 8; ++u) o[u] = *reinterpret_cast<const float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4));
+            epi.finish(b, mt, nt, row, c0, o, v);  // o: old -> new values; panels written
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 8; ++u) *reinterpret_cast<float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4)) = o[u];
+            nred = k + 1;  // the next plain box is the other one
+          } else {
+            // -acc of the warp's 32 rows x 32 columns as one swizzled box
+            // (row r, 16-byte chunk u at chunk u ^ (r & 7))
+            if (lane == 0) bulk_wait_read_n<kRedBuf - 1>();  // the box's previous operation has read it
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              *reinterpret_cast<float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4)) =
+                  make_float4(-v[4 * u], -v[4 * u + 1], -v[4 * u + 2], -v[4 * u + 3]);
+            ++nred;
+          }
+          // the box goes to the output by one tensor bulk operation: added at
+          // L2 (mode 0, no load on the SM) or stored (modes 1 and 2: the old
+          // values are dropped or already applied)
           fence_proxy_async();
-          bulk_reduce_add_f32(epi.row_ptr(b, mt, nt, row) + c0, srow, 128);
-          bulk_commit();
+          __syncwarp();
+          if (lane == 0) {
+            if (md == 0)
+              tma_reduce_add_2d(&epi.red_map, box, epi.red_x(nt, c0), epi.red_y(b, mt, q * 32));
+            else
+              tma_store_2d(&epi.red_map, box, epi.red_x(nt, c0), epi.red_y(b, mt, q * 32));
+            bulk_commit();
+          }
         } else {
           epi(b, mt, nt, row, c0, v);
         }
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
+    }
+    // no box load may be left in flight at exit (only after an abort)
+    for (int k = 0; k < kRedBuf; ++k) {
+      if (!(box_loading >> k & 1)) continue;
+      const uint64_t t0 = global_ns();
+      while (!mbar_test(&box_bar[k], (box_phase >> k) & 1) && global_ns() - t0 < kWaitNs) {
+      }
     }
     if (Epi::kStage) bulk_wait_all();
   }
@@ -352,7 +429,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1) umma_gemm_persistent_kernel
 
 template <class C, class Pairs, int EPIW, class Epi>
 int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
-  const int smem_bytes = C::kSmem + (Epi::kStage ? EPIW * 32 * 144 : 0);
+  const int smem_bytes = C::kSmem + (Epi::kStage ? red_stage_bytes<EPIW>() : 0);
   static bool attr = false;
   if (!attr) {
     NED_CUDA(cudaFuncSetAttribute(umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>,
@@ -396,54 +473,58 @@ struct EpiUpdate {
     if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return 1;
     return 0;
   }
-  __device__ float* row_ptr(int b, int mt, int nt, int r) const {
-    return A + b * bstride + (size_t)(mt * kTileRows + r) * 2 * np + nt * CfgGJ::kBn;
-  }
-  // warm L2 with the tile's 128 rows of old values (1 KB each)
+  // A of the whole batch as one FP32 tensor of 2 np columns and batch * np
+  // rows: red_map boxes 32 x 32 with 128-byte swizzle (the staged -acc),
+  // pre_map boxes of one tile, 256 x 128, for the L2 prefetch
+  CUtensorMap red_map, pre_map;
+  __device__ int red_x(int nt, int c0) const { return nt * CfgGJ::kBn + c0; }
+  __device__ int red_y(int b, int mt, int r0) const { return b * np + mt * kTileRows + r0; }
+  // warm L2 with the tile's old values
   __device__ void prefetch(int b, int mt, int nt) const {
     if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return;  // old values unused
-    const float* base = A + b * bstride + (size_t)(mt * kTileRows) * 2 * np + nt * CfgGJ::kBn;
-    for (int r = 0; r < kTileRows; ++r)
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + (size_t)r * 2 * np),
-                   "r"((uint32_t)(CfgGJ::kBn * sizeof(float)))
-                   : "memory");
+    tma_prefetch_2d(&pre_map, nt * CfgGJ::kBn, b * np + mt * kTileRows);
   }
-  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+  // mode 2 chunk of row r, real columns c0 .. c0+31 of the tile: o holds the
+  // old values and gets the new ones, old - acc (old values in block K
+  // dropped); the next step's panels are written from them
+  __device__ void finish(int b, int mt, int nt, int r, int c0, float4* o, const float* v) const {
     const int i = mt * kTileRows + r;
     const int n0 = nt * CfgGJ::kBn + c0;  // real column
-    float* row = A + b * bstride + (size_t)i * 2 * np + n0;
-    const bool ik = (i >= k0 && i < k0 + kNb);
-    const int j0 = n0 >> 1;  // first complex column of the chunk
-    const bool skip = ik || (nt * (CfgGJ::kBn / 2) == k0);  // the whole chunk lies in block K
-    float4 o[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      o[u] = skip ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(row + 4 * u);
+    const int j0 = n0 >> 1;               // first complex column of the chunk
+    const bool skip = (i >= k0 && i < k0 + kNb) || (nt * (CfgGJ::kBn / 2) == k0);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int ja = j0 + 2 * u;
-      if (ja >= k0 && ja < k0 + kNb) { o[u].x = 0.f; o[u].y = 0.f; }
-      if (ja + 1 >= k0 && ja + 1 < k0 + kNb) { o[u].z = 0.f; o[u].w = 0.f; }
+      if (skip || (ja >= k0 && ja < k0 + kNb)) { o[u].x = 0.f; o[u].y = 0.f; }
+      if (skip || (ja + 1 >= k0 && ja + 1 < k0 + kNb)) { o[u].z = 0.f; o[u].w = 0.f; }
       o[u].x -= v[4 * u]; o[u].y -= v[4 * u + 1]; o[u].z -= v[4 * u + 2]; o[u].w -= v[4 * u + 3];
-      *reinterpret_cast<float4*>(row + 4 * u) = o[u];
     }
     if (kn < 0) return;
     if (nt * (CfgGJ::kBn / 2) == kn) {
       // column block Kn: row i of C'_next (C'_Kn = -I)
+      // 4 complex values = one 16-byte core-matrix row per slice
       __nv_bfloat16* cd = cimg + b * pstride;
       const bool in = (i >= kn && i < kn + kNb);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int c = j0 + u - kn;
-        float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
-        float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
-        if (in) { re = (i - kn == c) ? -1.f : 0.f; im = 0.f; }
-        __nv_bfloat16 rh, rl, ih, il;
-        split2(re, rh, rl);
-        split2(im, ih, il);
-        const size_t off = img_offset(i, 2 * c, kKt);
-        *reinterpret_cast<__nv_bfloat162*>(cd + off) = __halves2bfloat162(rh, ih);
-        *reinterpret_cast<__nv_bfloat162*>(cd + cslice + off) = __halves2bfloat162(rl, il);
+      for (int g = 0; g < 4; ++g) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int u = 4 * g + e;
+          const int c = j0 + u - kn;
+          float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
+          float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
+          if (in) { re = (i - kn == c) ? -1.f : 0.f; im = 0.f; }
+          __nv_bfloat16 rh, rl, ih, il;
+          split2(re, rh, rl);
+          split2(im, ih, il);
+          const __nv_bfloat162 h2 = __halves2bfloat162(rh, ih), l2 = __halves2bfloat162(rl, il);
+          hi[e] = *reinterpret_cast<const uint32_t*>(&h2);
+          lo[e] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+        const size_t off = img_offset(i, 2 * (j0 + 4 * g - kn), kKt);  // 8-element aligned
+        *reinterpret_cast<uint4*>(cd + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(cd + cslice + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
     }
     if (mt * kTileRows == kn) {
@@ -475,7 +556,6 @@ struct EpiUpdate {
 struct EpiRPack {
   static constexpr bool kStage = false;
   __device__ int mode(int, int) const { return 1; }
-  __device__ float* row_ptr(int, int, int, int) const { return nullptr; }
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 kNb)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
@@ -648,6 +728,44 @@ GjBuffers gj_buffers(int np) {
 // Gauss-Jordan inversion of nb matrices (np x np FP32 complex, batch stride
 // np*np, np a multiple of 128) on the tensor cores.  `scratch` holds the
 // packed panels: gj_buffers(np) minus the matrix, times nb.
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once (no link against the driver library)
+EncodeTiledFn encode_tiled_fn() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of an FP32 matrix of `rows` rows of `cols` contiguous elements,
+// moved in boxes of box_cols x box_rows.
+int encode_f32_rows(CUtensorMap* map, float* base, uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows,
+                    CUtensorMapSwizzle swizzle) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * sizeof(float)};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t elem_strides[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, elem_strides,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return NEDMFT_OK;
+}
+
+}  // namespace
+
 int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st) {
   if (np % kNb) return set_error(NEDMFT_EINVAL, "gj_blocked_umma: np=%d not a multiple of %d", np, kNb);
   const GjBuffers g = gj_buffers(np);
@@ -662,6 +780,16 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
   // the C' / A_K^T panels alternate between two buffers: step k reads buffer
   // k & 1 while its update writes step k+1's panels into the other one
   const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
+  // A of the whole batch as one tensor of 2 np FP32 columns and nb np rows,
+  // for the update's staged bulk reductions and its L2 prefetch
+  CUtensorMap red_map, pre_map;
+  {
+    float* a = reinterpret_cast<float*>(A);
+    const uint64_t cols = 2 * (uint64_t)np, rows = (uint64_t)nb * np;
+    int rc = encode_f32_rows(&red_map, a, cols, rows, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (!rc) rc = encode_f32_rows(&pre_map, a, cols, rows, CfgGJ::kBn, kTileRows, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (rc) return rc;
+  }
   gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, 0, cimg, pstride, cslice, timg, pstride, tslice);
   NED_LAUNCH_CHECK("gj_panel_pack_kernel");
   for (int k0 = 0, step = 0; k0 < np; k0 += kNb, ++step) {
@@ -682,6 +810,8 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
       const int kn = (k0 + kNb < np) ? k0 + kNb : -1;
       EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
                     tslice};
+      epi.red_map = red_map;
+      epi.pre_map = pre_map;
       const int slot = instr_begin(st);
       int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
