@@ -29,8 +29,10 @@ Path choose_path(const nedmft_contour& c, nedmft_precision p) {
   return Path::MixedUmma;
 }
 
+int padded_for(Path path, int n) { return path == Path::MixedUmma ? umma_padded(n) : padded(n); }
+
 int default_batch(const nedmft_contour& c, int nq, Path path) {
-  const size_t np = padded(c.n_c);
+  const size_t np = padded_for(path, c.n_c);
   size_t per = 0, budget = (size_t)40 << 30;  // about 40 GB of batch buffers
   int cap = 152;
   switch (path) {
@@ -55,7 +57,7 @@ struct LatticeLayout {
 LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision prec, int batch) {
   LatticeLayout L{};
   L.path = choose_path(c, prec);
-  L.np = padded(c.n_c);
+  L.np = padded_for(L.path, c.n_c);
   L.mb = batch > 0 ? (batch < nq ? batch : nq) : default_batch(c, nq, L.path);
   const size_t n = c.n_c, np = L.np, mb = L.mb;
   L.S = align256(sizeof(double2) * n * n);

@@ -454,8 +454,32 @@ int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int ba
 
 // ------------------------------------------------------------------ epilogues
 
-// A <- A(rows K and columns K zeroed) - acc, A interleaved FP32 (row stride 2 np floats).
+__device__ __forceinline__ uint4 shfl_xor_u4(uint4 v, int m) {
+  return make_uint4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
+                    __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
+}
+// Within each quad of lanes (l = lane & 3): e[p] of lane l becomes lane p's
+// original e[l].  Step 1 transposes the 2 x 2 blocks of lane pairs, step 2
+// swaps the off-diagonal blocks.  Every lane of the warp must take part.
+__device__ __forceinline__ void quad_transpose4(uint4* e, int l) {
+  const bool b1 = l & 1, b2 = (l >> 1) & 1;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const uint4 r = shfl_xor_u4(b1 ? e[2 * g] : e[2 * g + 1], 1);
+    if (b1) e[2 * g] = r; else e[2 * g + 1] = r;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint4 r = shfl_xor_u4(b2 ? e[h] : e[2 + h], 2);
+    if (b2) e[h] = r; else e[2 + h] = r;
+  }
+}
+
+// A <- A(rows K and columns K zeroed) - acc, A interleaved FP32 (row stride 2
+// np floats), for a Gauss-Jordan block of W complex columns (W = 128, 256).
+template <int W>
 struct EpiUpdate {
+  static constexpr int kKtW = 2 * W / kTileK;  // K tiles of the rank-W products
   static constexpr bool kStage = true;
   float* A;
   size_t bstride;  // floats between matrices
@@ -468,9 +492,11 @@ struct EpiUpdate {
   // 0: plain tile, A += -acc by bulk reduction at L2; 1: rows or columns of
   // block K (new value = -acc); 2: the next step's panel blocks (new values
   // needed in registers)
+  // (a tile, 128 rows by 128 complex columns, lies wholly inside or outside a block)
+  __device__ static bool in_block(int x, int k) { return x >= k && x < k + W; }
   __device__ int mode(int mt, int nt) const {
-    if (kn >= 0 && (nt * (CfgGJ::kBn / 2) == kn || mt * kTileRows == kn)) return 2;
-    if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return 1;
+    if (kn >= 0 && (in_block(nt * (CfgGJ::kBn / 2), kn) || in_block(mt * kTileRows, kn))) return 2;
+    if (in_block(nt * (CfgGJ::kBn / 2), k0) || in_block(mt * kTileRows, k0)) return 1;
     return 0;
   }
   // A of the whole batch as one FP32 tensor of 2 np columns and batch * np
@@ -481,7 +507,7 @@ struct EpiUpdate {
   __device__ int red_y(int b, int mt, int r0) const { return b * np + mt * kTileRows + r0; }
   // warm L2 with the tile's old values
   __device__ void prefetch(int b, int mt, int nt) const {
-    if (nt * (CfgGJ::kBn / 2) == k0 || mt * kTileRows == k0) return;  // old values unused
+    if (in_block(nt * (CfgGJ::kBn / 2), k0) || in_block(mt * kTileRows, k0)) return;  // old values unused
     tma_prefetch_2d(&pre_map, nt * CfgGJ::kBn, b * np + mt * kTileRows);
   }
   // mode 2 chunk of row r, real columns c0 .. c0+31 of the tile: o holds the
@@ -491,20 +517,20 @@ struct EpiUpdate {
     const int i = mt * kTileRows + r;
     const int n0 = nt * CfgGJ::kBn + c0;  // real column
     const int j0 = n0 >> 1;               // first complex column of the chunk
-    const bool skip = (i >= k0 && i < k0 + kNb) || (nt * (CfgGJ::kBn / 2) == k0);
+    const bool skip = in_block(i, k0) || in_block(nt * (CfgGJ::kBn / 2), k0);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int ja = j0 + 2 * u;
-      if (skip || (ja >= k0 && ja < k0 + kNb)) { o[u].x = 0.f; o[u].y = 0.f; }
-      if (skip || (ja + 1 >= k0 && ja + 1 < k0 + kNb)) { o[u].z = 0.f; o[u].w = 0.f; }
+      if (skip || in_block(ja, k0)) { o[u].x = 0.f; o[u].y = 0.f; }
+      if (skip || in_block(ja + 1, k0)) { o[u].z = 0.f; o[u].w = 0.f; }
       o[u].x -= v[4 * u]; o[u].y -= v[4 * u + 1]; o[u].z -= v[4 * u + 2]; o[u].w -= v[4 * u + 3];
     }
     if (kn < 0) return;
-    if (nt * (CfgGJ::kBn / 2) == kn) {
+    if (in_block(nt * (CfgGJ::kBn / 2), kn)) {
       // column block Kn: row i of C'_next (C'_Kn = -I)
       // 4 complex values = one 16-byte core-matrix row per slice
       __nv_bfloat16* cd = cimg + b * pstride;
-      const bool in = (i >= kn && i < kn + kNb);
+      const bool in = in_block(i, kn);
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         uint32_t hi[4], lo[4];
@@ -522,46 +548,67 @@ struct EpiUpdate {
           hi[e] = *reinterpret_cast<const uint32_t*>(&h2);
           lo[e] = *reinterpret_cast<const uint32_t*>(&l2);
         }
-        const size_t off = img_offset(i, 2 * (j0 + 4 * g - kn), kKt);  // 8-element aligned
+        const size_t off = img_offset(i, 2 * (j0 + 4 * g - kn), kKtW);  // 8-element aligned
         *reinterpret_cast<uint4*>(cd + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(cd + cslice + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
     }
-    if (mt * kTileRows == kn) {
-      // row block Kn: row c = i - kn of A_{Kn,:}, embedded and transposed (A_{Kn,Kn} -> I)
+    if (in_block(mt * kTileRows, kn)) {
+      // row block Kn: row c = i - kn of A_{Kn,:}, embedded and transposed
+      // (A_{Kn,Kn} -> I): column j gives rows 2j, 2j+1 of the image at
+      // k = 2c, 2c+1.  A 16-byte core-matrix row holds k = 2c .. 2c+7 of one
+      // row, i.e. 4 consecutive c: each quad of lanes transposes its values
+      // (a 4 x 4 transpose of 16-byte elements in two xor exchanges) so that
+      // lane l of the quad writes whole rows of column j0 + 4 jq + l.
       __nv_bfloat16* td = timg + b * pstride;
       const int c = i - kn;
+      const int l = r & 3;
+      const int cq = c - l;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int j = j0 + u;
-        float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
-        float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
-        if (j >= kn && j < kn + kNb) { re = (j - kn == c) ? 1.f : 0.f; im = 0.f; }
-        __nv_bfloat16 rh, rl, ih, il, nh, nl;
-        split2(re, rh, rl);
-        split2(im, ih, il);
-        split2(-im, nh, nl);
-        const size_t o0 = img_offset(2 * j, 2 * c, kKt), o1 = img_offset(2 * j + 1, 2 * c, kKt);
-        *reinterpret_cast<__nv_bfloat162*>(td + o0) = __halves2bfloat162(rh, nh);
-        *reinterpret_cast<__nv_bfloat162*>(td + o1) = __halves2bfloat162(ih, rh);
-        *reinterpret_cast<__nv_bfloat162*>(td + tslice + o0) = __halves2bfloat162(rl, nl);
-        *reinterpret_cast<__nv_bfloat162*>(td + tslice + o1) = __halves2bfloat162(il, rl);
+      for (int jq = 0; jq < 4; ++jq) {
+        uint4 e[4];  // e[p]: (row 2j hi, row 2j+1 hi, row 2j lo, row 2j+1 lo) at k = 2c, j = j0 + 4 jq + p
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int u = 4 * jq + p;
+          const int j = j0 + u;
+          float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
+          float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
+          if (in_block(j, kn)) { re = (j - kn == c) ? 1.f : 0.f; im = 0.f; }
+          __nv_bfloat16 rh, rl, ih, il, nh, nl;
+          split2(re, rh, rl);
+          split2(im, ih, il);
+          split2(-im, nh, nl);
+          const __nv_bfloat162 a0 = __halves2bfloat162(rh, nh), a1 = __halves2bfloat162(ih, rh);
+          const __nv_bfloat162 a2 = __halves2bfloat162(rl, nl), a3 = __halves2bfloat162(il, rl);
+          e[p] = make_uint4(*reinterpret_cast<const uint32_t*>(&a0), *reinterpret_cast<const uint32_t*>(&a1),
+                            *reinterpret_cast<const uint32_t*>(&a2), *reinterpret_cast<const uint32_t*>(&a3));
+        }
+        quad_transpose4(e, l);  // e[m]: lane m's element for p = l
+        const int j = j0 + 4 * jq + l;
+        const size_t o0 = img_offset(2 * j, 2 * cq, kKtW), o1 = img_offset(2 * j + 1, 2 * cq, kKtW);
+        *reinterpret_cast<uint4*>(td + o0) = make_uint4(e[0].x, e[1].x, e[2].x, e[3].x);
+        *reinterpret_cast<uint4*>(td + o1) = make_uint4(e[0].y, e[1].y, e[2].y, e[3].y);
+        *reinterpret_cast<uint4*>(td + tslice + o0) = make_uint4(e[0].z, e[1].z, e[2].z, e[3].z);
+        *reinterpret_cast<uint4*>(td + tslice + o1) = make_uint4(e[0].w, e[1].w, e[2].w, e[3].w);
       }
     }
   }
 };
 
-// R (kNb x np complex, acc rows = R rows) -> the update's B operand image:
+// R (W x np complex, acc rows = R rows) -> the update's B operand image:
 // rows n = 2j, 2j+1; k = 2r, 2r+1 with [[re, -im], [im, re]].
+template <int W>
 struct EpiRPack {
   static constexpr bool kStage = false;
+  static constexpr int kKtW = 2 * W / kTileK;
   __device__ int mode(int, int) const { return 1; }
-  __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 kNb)
+  __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 W)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
   __device__ void prefetch(int, int, int) const {}
-  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+  __device__ void operator()(int b, int mt, int nt, int r_tile, int c0, const float* v) const {
     __nv_bfloat16* base = img + b * bstride;
+    const int r = mt * kTileRows + r_tile;  // row of R
     const int n0 = nt * CfgGJ::kBn + c0;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
@@ -571,8 +618,8 @@ struct EpiRPack {
       split2(re, rh, rl);
       split2(im, ih, il);
       split2(-im, nh, nl);
-      const size_t o0 = img_offset(2 * j, 2 * r, kKt);      // (re, -im)
-      const size_t o1 = img_offset(2 * j + 1, 2 * r, kKt);  // (im, re)
+      const size_t o0 = img_offset(2 * j, 2 * r, kKtW);      // (re, -im)
+      const size_t o1 = img_offset(2 * j + 1, 2 * r, kKtW);  // (im, re)
       *reinterpret_cast<__nv_bfloat162*>(base + o0) = __halves2bfloat162(rh, nh);
       *reinterpret_cast<__nv_bfloat162*>(base + o1) = __halves2bfloat162(ih, rh);
       *reinterpret_cast<__nv_bfloat162*>(base + slice + o0) = __halves2bfloat162(rl, nl);
@@ -659,8 +706,39 @@ __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __res
     }
 }
 
+// Copy of the W x W diagonal block A_KK of every matrix (inverted in place by
+// the W = 128 Gauss-Jordan when the outer block is wider).
+template <int W>
+__global__ void __launch_bounds__(256) gj_extract_kernel(const float2* __restrict__ A, int np, int k0,
+                                                         float2* __restrict__ out) {
+  const int b = blockIdx.y, r = blockIdx.x;
+  const float2* src = A + (size_t)b * np * np + (size_t)(k0 + r) * np + k0;
+  float2* dst = out + ((size_t)b * W + r) * W;
+  for (int c = threadIdx.x; c < W; c += blockDim.x) dst[c] = src[c];
+}
+
+// P = inv(A_KK) (W x W, FP32) as the R-product's A operand: row r, k = 2c / 2c+1.
+template <int W>
+__global__ void __launch_bounds__(256) gj_ppack_kernel(const float2* __restrict__ Pinv, __nv_bfloat16* __restrict__ pimg,
+                                                       size_t pstride, size_t pslice) {
+  const int b = blockIdx.y, r = blockIdx.x;
+  const float2* src = Pinv + ((size_t)b * W + r) * W;
+  __nv_bfloat16* dst = pimg + b * pstride;
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    const float2 z = src[c];
+    __nv_bfloat16 rh, rl, ih, il;
+    split2(z.x, rh, rl);
+    split2(z.y, ih, il);
+    const size_t o = img_offset(r, 2 * c, 2 * W / kTileK);
+    *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
+    *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
+  }
+}
+
 // Block x of matrix y: rows x*128 .. +127 of C' (the update's A operand) and
-// columns x*128 .. +127 of the embedded A_{K,:}^T (the R-product's B operand).
+// columns x*128 .. +127 of the embedded A_{K,:}^T (the R-product's B operand),
+// for a block K of W columns.
+template <int W>
 __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __restrict__ A, int np, int k0,
                                                             __nv_bfloat16* __restrict__ cimg, size_t cstride,
                                                             size_t cslice, __nv_bfloat16* __restrict__ timg,
@@ -670,17 +748,17 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
   const float2* src = A + (size_t)b * np * np;
   __nv_bfloat16* cd = cimg + b * cstride;
   __nv_bfloat16* td = timg + b * tstride;
-  for (int e = threadIdx.x; e < 128 * kNb; e += blockDim.x) {
-    // C'[i][c], i = base + e / kNb, c = e % kNb (consecutive threads: consecutive c)
+  for (int e = threadIdx.x; e < 128 * W; e += blockDim.x) {
+    // C'[i][c], i = base + e / W, c = e % W (consecutive threads: consecutive c)
     {
-      const int i = base + e / kNb, c = e % kNb;
+      const int i = base + e / W, c = e % W;
       float2 z;
-      if (i >= k0 && i < k0 + kNb) z = make_float2(i - k0 == c ? -1.f : 0.f, 0.f);
+      if (i >= k0 && i < k0 + W) z = make_float2(i - k0 == c ? -1.f : 0.f, 0.f);
       else z = src[(size_t)i * np + k0 + c];
       __nv_bfloat16 rh, rl, ih, il;
       split2(z.x, rh, rl);
       split2(z.y, ih, il);
-      const size_t o = img_offset(i, 2 * c, kKt);
+      const size_t o = img_offset(i, 2 * c, 2 * W / kTileK);
       *reinterpret_cast<__nv_bfloat162*>(cd + o) = __halves2bfloat162(rh, ih);
       *reinterpret_cast<__nv_bfloat162*>(cd + cslice + o) = __halves2bfloat162(rl, il);
     }
@@ -688,14 +766,14 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
     {
       const int j = base + (e & 127), c = e >> 7;
       float2 z;
-      if (j >= k0 && j < k0 + kNb) z = make_float2(j - k0 == c ? 1.f : 0.f, 0.f);
+      if (j >= k0 && j < k0 + W) z = make_float2(j - k0 == c ? 1.f : 0.f, 0.f);
       else z = src[(size_t)(k0 + c) * np + j];
       __nv_bfloat16 rh, rl, ih, il, nh, nl;
       split2(z.x, rh, rl);
       split2(z.y, ih, il);
       split2(-z.y, nh, nl);
-      const size_t o0 = img_offset(2 * j, 2 * c, kKt);
-      const size_t o1 = img_offset(2 * j + 1, 2 * c, kKt);
+      const size_t o0 = img_offset(2 * j, 2 * c, 2 * W / kTileK);
+      const size_t o1 = img_offset(2 * j + 1, 2 * c, 2 * W / kTileK);
       *reinterpret_cast<__nv_bfloat162*>(td + o0) = __halves2bfloat162(rh, nh);
       *reinterpret_cast<__nv_bfloat162*>(td + o1) = __halves2bfloat162(ih, rh);
       *reinterpret_cast<__nv_bfloat162*>(td + tslice + o0) = __halves2bfloat162(rl, nl);
@@ -707,27 +785,41 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
 // ------------------------------------------------------------------ buffer layout per matrix
 
 struct GjBuffers {
-  size_t mat, pimg, cimg, timg, rimg, total;  // bytes, each 1024-aligned; cimg / timg hold two panels each
+  // bytes per matrix, each 1024-aligned; cimg / timg hold two panels each;
+  // inner: for W = 256, the copy of A_KK and the W = 128 scratch that inverts it
+  size_t mat, pimg, cimg, timg, rimg, inner, scratch, total;
 };
 
 size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
+template <int W>
 GjBuffers gj_buffers(int np) {
   GjBuffers g{};
   g.mat = align1k(sizeof(float2) * (size_t)np * np);
-  g.pimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)kNb * 2 * kNb);
-  g.cimg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * kNb);
-  g.timg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * kNb);
+  g.pimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)W * 2 * W);
+  g.cimg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);
+  g.timg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * W);
   g.rimg = g.timg / 2;
-  g.total = g.mat + g.pimg + g.cimg + g.timg + g.rimg;
+  if constexpr (W > 128) {
+    const GjBuffers in = gj_buffers<128>(W);
+    g.inner = in.mat + in.scratch;
+  }
+  g.scratch = g.pimg + g.cimg + g.timg + g.rimg + g.inner;
+  g.total = g.mat + g.scratch;
   return g;
 }
+
+// Block width of the tensor-core Gauss-Jordan for padded size np.
+int gj_width(int np) { return (np >= 512 && np % 256 == 0) ? 256 : 128; }
+
+GjBuffers gj_buffers_for(int np) { return gj_width(np) == 256 ? gj_buffers<256>(np) : gj_buffers<128>(np); }
 
 }  // namespace
 
 // Gauss-Jordan inversion of nb matrices (np x np FP32 complex, batch stride
-// np*np, np a multiple of 128) on the tensor cores.  `scratch` holds the
-// packed panels: gj_buffers(np) minus the matrix, times nb.
+// np*np, np a multiple of 128) on the tensor cores, in blocks of W = 128 or
+// 256 columns (256 for np >= 512 and a multiple of 256).  `scratch` holds
+// gj_buffers_for(np).scratch bytes per matrix.
 namespace {
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -766,17 +858,24 @@ int encode_f32_rows(CUtensorMap* map, float* base, uint64_t cols, uint64_t rows,
 
 }  // namespace
 
-int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st) {
-  if (np % kNb) return set_error(NEDMFT_EINVAL, "gj_blocked_umma: np=%d not a multiple of %d", np, kNb);
-  const GjBuffers g = gj_buffers(np);
+namespace {
+
+template <int W>
+int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st,
+                      bool instrument) {
+  if (np % W) return set_error(NEDMFT_EINVAL, "gj_blocked_umma: np=%d not a multiple of %d", np, W);
+  constexpr int kKtW = 2 * W / kTileK;
+  const GjBuffers g = gj_buffers<W>(np);
+  // per matrix b: scratch + b * per holds its pimg | cimg | timg | rimg;
+  // after the nb of those, the inner regions (W = 256)
   const size_t per = g.pimg + g.cimg + g.timg + g.rimg;
   __nv_bfloat16* pimg = reinterpret_cast<__nv_bfloat16*>(scratch);
   __nv_bfloat16* cimg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg);
   __nv_bfloat16* timg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg + g.cimg);
   __nv_bfloat16* rimg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg + g.cimg + g.timg);
-  const size_t pstride = per / 2, pslice = (size_t)kNb * 2 * kNb;
-  const size_t cslice = (size_t)np * 2 * kNb;
-  const size_t tslice = (size_t)2 * np * 2 * kNb;
+  const size_t pstride = per / 2, pslice = (size_t)W * 2 * W;
+  const size_t cslice = (size_t)np * 2 * W;
+  const size_t tslice = (size_t)2 * np * 2 * W;
   // the C' / A_K^T panels alternate between two buffers: step k reads buffer
   // k & 1 while its update writes step k+1's panels into the other one
   const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
@@ -790,36 +889,60 @@ int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status
     if (!rc) rc = encode_f32_rows(&pre_map, a, cols, rows, CfgGJ::kBn, kTileRows, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (rc) return rc;
   }
-  gj_panel_pack_kernel<<<dim3(np / 128, nb), 256, 0, st>>>(A, np, 0, cimg, pstride, cslice, timg, pstride, tslice);
+  gj_panel_pack_kernel<W>
+      <<<dim3(np / 128, nb), 256, 0, st>>>(A, np, 0, cimg, pstride, cslice, timg, pstride, tslice);
   NED_LAUNCH_CHECK("gj_panel_pack_kernel");
-  for (int k0 = 0, step = 0; k0 < np; k0 += kNb, ++step) {
+  for (int k0 = 0, step = 0; k0 < np; k0 += W, ++step) {
     __nv_bfloat16* cur_c = cimg + (step & 1) * chalf;
     __nv_bfloat16* cur_t = timg + (step & 1) * thalf;
     __nv_bfloat16* nxt_c = cimg + ((step + 1) & 1) * chalf;
     __nv_bfloat16* nxt_t = timg + ((step + 1) & 1) * thalf;
-    gj_pivot_pack_kernel<<<nb, 1024, 0, st>>>(A, np, k0, pimg, pstride, pslice, status);
-    NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
-    {  // R = P A_{K,:}, 128 x 2np, K = 256
-      GemmParams p{pimg, pstride, pslice, cur_t, pstride, tslice, kKt, status};
-      EpiRPack epi{rimg, pstride, tslice};
-      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, 1, nb, epi, st);
+    if constexpr (W == 128) {
+      gj_pivot_pack_kernel<<<nb, 1024, 0, st>>>(A, np, k0, pimg, pstride, pslice, status);
+      NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
+    } else {
+      // P = inv(A_KK): the W = 128 Gauss-Jordan on copies of the diagonal blocks
+      char* inner = scratch + per * nb;
+      float2* Xs = reinterpret_cast<float2*>(inner);
+      char* inner_scratch = inner + gj_buffers<128>(W).mat * nb;
+      gj_extract_kernel<W><<<dim3(W, nb), 256, 0, st>>>(A, np, k0, Xs);
+      NED_LAUNCH_CHECK("gj_extract_kernel");
+      int rc = gj_blocked_umma_w<128>(Xs, W, W, nb, inner_scratch, status, st, false);
+      if (rc) return rc;
+      gj_ppack_kernel<W><<<dim3(W, nb), 256, 0, st>>>(Xs, pimg, pstride, pslice);
+      NED_LAUNCH_CHECK("gj_ppack_kernel");
+    }
+    {  // R = P A_{K,:}, W x 2np, K = 2W
+      GemmParams p{pimg, pstride, pslice, cur_t, pstride, tslice, kKtW, status};
+      EpiRPack<W> epi{rimg, pstride, tslice};
+      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, W / kTileRows, nb, epi, st);
       if (rc) return rc;
     }
-    {  // A <- A - C' R, np x 2np, K = 256; next step's panels from the epilogue
-      GemmParams p{cur_c, pstride, cslice, rimg, pstride, tslice, kKt, status};
-      const int kn = (k0 + kNb < np) ? k0 + kNb : -1;
-      EpiUpdate epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
-                    tslice};
+    {  // A <- A - C' R, np x 2np, K = 2W; next step's panels from the epilogue
+      GemmParams p{cur_c, pstride, cslice, rimg, pstride, tslice, kKtW, status};
+      const int kn = (k0 + W < np) ? k0 + W : -1;
+      EpiUpdate<W> epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
+                       tslice};
       epi.red_map = red_map;
       epi.pre_map = pre_map;
-      const int slot = instr_begin(st);
+      const int slot = instrument ? instr_begin(st) : -1;
       int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
-      const int live = n - k0 < kNb ? (n - k0 > 0 ? n - k0 : 0) : kNb;
-      instr_end(slot, st, 8.0 * (double)n * n * live * nb, live > 0 ? 2.0 * sizeof(float2) * (double)n * n * nb : 0.0);
+      if (instrument) {
+        const int live = n - k0 < W ? (n - k0 > 0 ? n - k0 : 0) : W;
+        instr_end(slot, st, 8.0 * (double)n * n * live * nb,
+                  live > 0 ? 2.0 * sizeof(float2) * (double)n * n * nb : 0.0);
+      }
     }
   }
   return NEDMFT_OK;
+}
+
+}  // namespace
+
+int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st) {
+  return gj_width(np) == 256 ? gj_blocked_umma_w<256>(A, n, np, nb, scratch, status, st, true)
+                             : gj_blocked_umma_w<128>(A, n, np, nb, scratch, status, st, true);
 }
 
 // ------------------------------------------------------------------ refinement
@@ -1438,13 +1561,14 @@ size_t flags_bytes(int nq) { return align1k(sizeof(int) * (size_t)nq); }
 
 // ------------------------------------------------------------------ lattice batch on this path
 
-size_t umma_batch_bytes_per_matrix(int np) { return gj_buffers(np).total + refine_layout(np, 1).total; }
+int umma_padded(int n) { return n > 512 ? ((n + 255) / 256) * 256 : ((n + 127) / 128) * 128; }
+size_t umma_batch_bytes_per_matrix(int np) { return gj_buffers_for(np).total + refine_layout(np, 1).total; }
 int umma_default_batch(int np) { return np <= 2048 ? 152 : 76; }
 size_t umma_shared_bytes(int np, int nq) {
   return align1k(kOzS * sizeof(__nv_bfloat16) * (size_t)np * 2 * np) + align1k(sizeof(int) * (size_t)np) +
          flags_bytes(nq) + align1k(sizeof(float2) * (size_t)np * np);
 }
-size_t umma_batch_bytes(int np, int nb) { return gj_buffers(np).total * nb + refine_layout(np, nb).total; }
+size_t umma_batch_bytes(int np, int nb) { return gj_buffers_for(np).total * nb + refine_layout(np, nb).total; }
 
 int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
                         const double* wq, int nq, char* shared, cudaStream_t st) {
@@ -1461,16 +1585,15 @@ int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const dou
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
                        const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
                        char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
-  const GjBuffers g = gj_buffers(np);
+  const GjBuffers g = gj_buffers_for(np);
   const RefineShared sh = shared_layout(shared, np, nq_total);
   const int mb_alloc = nb;  // regions are sized for this batch by the caller's layout
   (void)mb_alloc;
   // layout: nb matrices | nb GJ panel scratch | refinement regions
   float2* X = reinterpret_cast<float2*>(batch);
   char* scratch = batch + g.mat * nb;
-  const size_t per = g.pimg + g.cimg + g.timg + g.rimg;
   const RefineLayout rl = refine_layout(np, nb);
-  char* rbase = scratch + per * nb;
+  char* rbase = scratch + g.scratch * nb;
   __nv_bfloat16* ximg = reinterpret_cast<__nv_bfloat16*>(rbase);
   int* xexp = reinterpret_cast<int*>(rbase + rl.ximg);
   __nv_bfloat16* aimg = reinterpret_cast<__nv_bfloat16*>(rbase + rl.ximg + rl.xexp);

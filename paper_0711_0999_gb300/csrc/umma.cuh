@@ -6,6 +6,8 @@
 
 namespace nedmft {
 
+// padded size for this path: a multiple of 128, of 256 above 512 (wider Gauss-Jordan blocks)
+int umma_padded(int n);
 size_t umma_batch_bytes_per_matrix(int np);
 size_t umma_batch_bytes(int np, int nb);
 int umma_default_batch(int np);

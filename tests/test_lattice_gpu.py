@@ -95,6 +95,20 @@ def test_lattice_ragged_blocked(prec):
     assert np.abs(j - jref.real).max() < tj
 
 
+@pytest.mark.parametrize("args,n_c", [((-2, 8, 0.05, 5.0, 0.1), 450), ((-2, 14.5, 0.05, 4.0, 0.1), 700)])
+def test_lattice_wide_gauss_jordan_blocks(args, n_c):
+    # padded sizes 512 and 768: the tensor-core Gauss-Jordan runs in blocks of
+    # 256 columns (2 and 3 steps, each pivot block inverted by the 128 blocks)
+    c, g, mo, mc, sig, eps, ebar, wq = setup(args, 1.0, 1.5, 4, seed=11)
+    assert c.n_c == n_c
+    ref, jref = O.lattice_gloc(c, mo, sig, eps, ebar, wq)
+    gl, j, ji = run_gpu(g, mc, sig, eps, ebar, wq, "mixed_bf16")
+    tg, tj = TOL["mixed_bf16"]
+    assert rel(gl, ref) < tg
+    assert np.abs(j - jref.real).max() < tj
+    assert np.abs(ji - jref.imag).max() < tj
+
+
 def test_lattice_many_batches_fp64():
     # more points than one batch of the blocked FP64 path (152), N_c = 130
     c, g, mo, mc, sig, eps, ebar, wq = setup((-1, 2, 0.05, 1.0, 0.1), 1.0, 1.0, 13, seed=9)
