@@ -630,56 +630,73 @@ struct EpiRPack {
 
 // ------------------------------------------------------------------ panel kernels (CUDA cores)
 
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat16 a, __nv_bfloat16 b) {
+  const __nv_bfloat162 v = __halves2bfloat162(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // P = inv(A_KK) (kNb x kNb, FP32, no pivoting -- the static row order makes
 // the pivots safe) written as the R-product's A operand: row r, k = 2c / 2c+1.
-// 1024 threads, each holding a 4 x 4 block of A_KK in registers; step k
-// broadcasts row k and column k through double-buffered shared memory.
-__global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
-                                                             __nv_bfloat16* __restrict__ pimg, size_t pstride,
-                                                             size_t pslice, int* status) {
-  __shared__ float2 rowb[2][kNb], colb[2][kNb];
-  const int b = blockIdx.x;
+// A_KK sits in shared memory and is inverted in two 64-column halves (block
+// Gauss-Jordan):
+//   B11 <- P1 = inv(A11);  B12 <- P1 A12;  B22 <- A22 - A21 B12;  B21 <- -A21 P1;
+//   B22 <- X22 = inv(B22); V = -B12 X22;  B21 <- X22 B21;  B11 <- P1 + V B21(old);  B12 <- V,
+// the two 64 x 64 inversions unblocked (one barrier per pivot, 2 x 2 complex
+// entries per thread), the products by all 1024 threads (1 x 4 outputs each).
+constexpr int kPivH = kNb / 2;
+constexpr size_t kPivSmem = (size_t)(kNb * kNb + kPivH * kPivH) * sizeof(float2);  // 160 KB
+
+struct PivShared {
+  float2 rowb[2][kPivH], colb[2][kPivH], pivb[2];
+  int bad;
+};
+
+// unblocked in-place Gauss-Jordan of the 64 x 64 block of M (row stride kNb) at (o, o)
+__device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
   const int t = threadIdx.x;
-  const int r0 = 4 * (t >> 5), c0 = 4 * (t & 31);
-  const float2* src = A + (size_t)b * np * np;
-  float2 a[4][4];
+  const int rr = 2 * (t >> 5), cc = 2 * (t & 31);
+  float2 a[2][2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4* p = reinterpret_cast<const float4*>(src + (size_t)(k0 + r0 + i) * np + k0 + c0);
-    const float4 u = p[0], v = p[1];
-    a[i][0] = make_float2(u.x, u.y); a[i][1] = make_float2(u.z, u.w);
-    a[i][2] = make_float2(v.x, v.y); a[i][3] = make_float2(v.z, v.w);
-  }
-  bool bad = false;
-  for (int k = 0; k < kNb; ++k) {
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) a[i][j] = M[(o + rr + i) * kNb + o + cc + j];
+  for (int k = 0; k < kPivH; ++k) {
     const int buf = k & 1;
-    if ((k >> 2) == (r0 >> 2)) {
+    const bool row_k = (k >> 1) == (rr >> 1), col_k = (k >> 1) == (cc >> 1);
+    if (row_k) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (r0 + i == k)
+      for (int i = 0; i < 2; ++i)
+        if (rr + i == k) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) rowb[buf][c0 + j] = a[i][j];
+          for (int j = 0; j < 2; ++j) {
+            sh.rowb[buf][cc + j] = a[i][j];
+            if (cc + j == k) {
+              float2 pinv;
+              if (!cinv_guard<float>(a[i][j], pinv, 1e-6f)) sh.bad = 1;
+              sh.pivb[buf] = pinv;
+            }
+          }
+        }
     }
-    if ((k >> 2) == (c0 >> 2)) {
+    if (col_k) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (c0 + j == k)
+      for (int j = 0; j < 2; ++j)
+        if (cc + j == k)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) colb[buf][r0 + i] = a[i][j];
+          for (int i = 0; i < 2; ++i) sh.colb[buf][rr + i] = a[i][j];
     }
     __syncthreads();
-    float2 pinv;
-    bad |= !cinv_guard<float>(rowb[buf][k], pinv, 1e-6f);
-    float2 rk[4], g[4];
+    const float2 pinv = sh.pivb[buf];
+    float2 rk[2], g[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) rk[j] = rowb[buf][c0 + j];
+    for (int j = 0; j < 2; ++j) rk[j] = sh.rowb[buf][cc + j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) g[i] = cmul(colb[buf][r0 + i], pinv);
+    for (int i = 0; i < 2; ++i) g[i] = cmul(sh.colb[buf][rr + i], pinv);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = r0 + i, c = c0 + j;
+      for (int j = 0; j < 2; ++j) {
+        const int r = rr + i, c = cc + j;
         if (r == k) {
           a[i][j] = (c == k) ? pinv : cmul(rk[j], pinv);
         } else if (c == k) {
@@ -689,21 +706,132 @@ __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __res
           a[i][j].y -= g[i].x * rk[j].y + g[i].y * rk[j].x;
         }
       }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) M[(o + rr + i) * kNb + o + cc + j] = a[i][j];
+}
+
+// acc[q] = sum_k X[i][k] Y[k][j0 + q] over 64 x 64 blocks (row strides ldx, ldy),
+// i = t / 16, j0 = 4 (t % 16)
+__device__ __forceinline__ void piv_gemm64(const float2* X, int ldx, const float2* Y, int ldy, float2* acc) {
+  const int t = threadIdx.x;
+  const int i = t >> 4, j0 = 4 * (t & 15);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll 8
+  for (int k = 0; k < kPivH; ++k) {
+    const float2 x = X[i * ldx + k];
+    const float4 y01 = *reinterpret_cast<const float4*>(Y + k * ldy + j0);
+    const float4 y23 = *reinterpret_cast<const float4*>(Y + k * ldy + j0 + 2);
+    const float2 y[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w), make_float2(y23.x, y23.y),
+                         make_float2(y23.z, y23.w)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[q].x += x.x * y[q].x - x.y * y[q].y;
+      acc[q].y += x.x * y[q].y + x.y * y[q].x;
     }
   }
-  if (bad && t == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
+}
+__device__ __forceinline__ void piv_put(float2* Z, int ldz, const float2* v) {
+  const int t = threadIdx.x;
+  const int i = t >> 4, j0 = 4 * (t & 15);
+  *reinterpret_cast<float4*>(Z + i * ldz + j0) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  *reinterpret_cast<float4*>(Z + i * ldz + j0 + 2) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void piv_get(const float2* Z, int ldz, float2* v) {
+  const int t = threadIdx.x;
+  const int i = t >> 4, j0 = 4 * (t & 15);
+  const float4 a = *reinterpret_cast<const float4*>(Z + i * ldz + j0);
+  const float4 b = *reinterpret_cast<const float4*>(Z + i * ldz + j0 + 2);
+  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+
+__global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
+                                                             __nv_bfloat16* __restrict__ pimg, size_t pstride,
+                                                             size_t pslice, int* status) {
+  extern __shared__ __align__(16) float2 piv_smem[];
+  __shared__ PivShared sh;
+  float2* M = piv_smem;               // A_KK, row stride kNb
+  float2* T = piv_smem + kNb * kNb;   // 64 x 64 temporary
+  float2* B11 = M;
+  float2* B12 = M + kPivH;
+  float2* B21 = M + kPivH * kNb;
+  float2* B22 = M + kPivH * kNb + kPivH;
+  const int b = blockIdx.x;
+  const int t = threadIdx.x;
+  const float2* src = A + (size_t)b * np * np;
+  for (int e = t; e < kNb * kNb / 2; e += blockDim.x) {
+    const int r = e / (kNb / 2), v = e % (kNb / 2);
+    *reinterpret_cast<float4*>(M + r * kNb + 2 * v) =
+        *reinterpret_cast<const float4*>(src + (size_t)(k0 + r) * np + k0 + 2 * v);
+  }
+  if (t == 0) sh.bad = 0;
+  __syncthreads();
+  float2 u[4], w[4];
+  piv_gj64(M, 0, sh);  // B11 <- P1
+  __syncthreads();
+  piv_gemm64(B11, kNb, B12, kNb, u);  // P1 A12
+  __syncthreads();
+  piv_put(B12, kNb, u);
+  __syncthreads();
+  piv_gemm64(B21, kNb, B12, kNb, u);  // A21 B12
+  piv_gemm64(B21, kNb, B11, kNb, w);  // A21 P1
+  {
+    float2 z[4];
+    piv_get(B22, kNb, z);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { z[q].x -= u[q].x; z[q].y -= u[q].y; w[q].x = -w[q].x; w[q].y = -w[q].y; }
+    __syncthreads();
+    piv_put(B22, kNb, z);
+    piv_put(B21, kNb, w);
+  }
+  __syncthreads();
+  piv_gj64(M, kPivH, sh);  // B22 <- X22
+  __syncthreads();
+  piv_gemm64(B12, kNb, B22, kNb, u);  // B12 X22
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { u[q].x = -u[q].x; u[q].y = -u[q].y; }
+  piv_put(T, kPivH, u);  // V
+  __syncthreads();
+  piv_gemm64(B22, kNb, B21, kNb, u);  // X22 B21
+  piv_gemm64(T, kPivH, B21, kNb, w);  // V B21
+  {
+    float2 p1[4], v[4];
+    piv_get(B11, kNb, p1);
+    piv_get(T, kPivH, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { w[q].x += p1[q].x; w[q].y += p1[q].y; }
+    __syncthreads();
+    piv_put(B21, kNb, u);
+    piv_put(B11, kNb, w);
+    piv_put(B12, kNb, v);
+  }
+  __syncthreads();
+  if (sh.bad && t == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
+  // row r, k = 2c .. 2c + 31 for c = 16 g .. 16 g + 15: four 16-byte core-matrix rows per slice
   __nv_bfloat16* dst = pimg + b * pstride;
+  {
+    const int r = t >> 3, cg = 16 * (t & 7);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int h = 0; h < 4; ++h) {
+      uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat16 rh, rl, ih, il;
-      split2(a[i][j].x, rh, rl);
-      split2(a[i][j].y, ih, il);
-      const size_t o = img_offset(r0 + i, 2 * (c0 + j), kKt);
-      *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
-      *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
+      for (int q = 0; q < 4; ++q) {
+        const float2 z = M[r * kNb + cg + 4 * h + q];
+        __nv_bfloat16 rh, rl, ih, il;
+        split2(z.x, rh, rl);
+        split2(z.y, ih, il);
+        hi[q] = bf2_bits(rh, ih);
+        lo[q] = bf2_bits(rl, il);
+      }
+      const size_t o = img_offset(r, 2 * (cg + 4 * h), kKt);
+      *reinterpret_cast<uint4*>(dst + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(dst + pslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+  }
 }
 
 // Copy of the W x W diagonal block A_KK of every matrix (inverted in place by
@@ -737,47 +865,60 @@ __global__ void __launch_bounds__(256) gj_ppack_kernel(const float2* __restrict_
 
 // Block x of matrix y: rows x*128 .. +127 of C' (the update's A operand) and
 // columns x*128 .. +127 of the embedded A_{K,:}^T (the R-product's B operand),
-// for a block K of W columns.
+// for a block K of W columns.  A thread takes 4 consecutive columns c of C'
+// (one 16-byte core-matrix row per slice) or 4 consecutive rows c of A_{K,:}
+// at one column j (consecutive threads: consecutive j, coalesced loads).
 template <int W>
 __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __restrict__ A, int np, int k0,
                                                             __nv_bfloat16* __restrict__ cimg, size_t cstride,
                                                             size_t cslice, __nv_bfloat16* __restrict__ timg,
                                                             size_t tstride, size_t tslice) {
+  constexpr int kKtW = 2 * W / kTileK;
+  constexpr int G = W / 4;
   const int b = blockIdx.y;
   const int base = blockIdx.x * 128;
   const float2* src = A + (size_t)b * np * np;
   __nv_bfloat16* cd = cimg + b * cstride;
   __nv_bfloat16* td = timg + b * tstride;
-  for (int e = threadIdx.x; e < 128 * W; e += blockDim.x) {
-    // C'[i][c], i = base + e / W, c = e % W (consecutive threads: consecutive c)
-    {
-      const int i = base + e / W, c = e % W;
-      float2 z;
-      if (i >= k0 && i < k0 + W) z = make_float2(i - k0 == c ? -1.f : 0.f, 0.f);
-      else z = src[(size_t)i * np + k0 + c];
-      __nv_bfloat16 rh, rl, ih, il;
-      split2(z.x, rh, rl);
-      split2(z.y, ih, il);
-      const size_t o = img_offset(i, 2 * c, 2 * W / kTileK);
-      *reinterpret_cast<__nv_bfloat162*>(cd + o) = __halves2bfloat162(rh, ih);
-      *reinterpret_cast<__nv_bfloat162*>(cd + cslice + o) = __halves2bfloat162(rl, il);
+  for (int e = threadIdx.x; e < 128 * G; e += blockDim.x) {
+    {  // C'[i][c4 .. c4+3]
+      const int i = base + e / G, c4 = 4 * (e % G);
+      const bool in = (i >= k0 && i < k0 + W);
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 z = in ? make_float2(i - k0 == c4 + q ? -1.f : 0.f, 0.f) : src[(size_t)i * np + k0 + c4 + q];
+        __nv_bfloat16 rh, rl, ih, il;
+        split2(z.x, rh, rl);
+        split2(z.y, ih, il);
+        hi[q] = bf2_bits(rh, ih);
+        lo[q] = bf2_bits(rl, il);
+      }
+      const size_t o = img_offset(i, 2 * c4, kKtW);
+      *reinterpret_cast<uint4*>(cd + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(cd + cslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
-    // T[n][k]: column j = base + e % 128 of A_{K,:}, row c = e / 128
-    {
-      const int j = base + (e & 127), c = e >> 7;
-      float2 z;
-      if (j >= k0 && j < k0 + W) z = make_float2(j - k0 == c ? 1.f : 0.f, 0.f);
-      else z = src[(size_t)(k0 + c) * np + j];
-      __nv_bfloat16 rh, rl, ih, il, nh, nl;
-      split2(z.x, rh, rl);
-      split2(z.y, ih, il);
-      split2(-z.y, nh, nl);
-      const size_t o0 = img_offset(2 * j, 2 * c, 2 * W / kTileK);
-      const size_t o1 = img_offset(2 * j + 1, 2 * c, 2 * W / kTileK);
-      *reinterpret_cast<__nv_bfloat162*>(td + o0) = __halves2bfloat162(rh, nh);
-      *reinterpret_cast<__nv_bfloat162*>(td + o1) = __halves2bfloat162(ih, rh);
-      *reinterpret_cast<__nv_bfloat162*>(td + tslice + o0) = __halves2bfloat162(rl, nl);
-      *reinterpret_cast<__nv_bfloat162*>(td + tslice + o1) = __halves2bfloat162(il, rl);
+    {  // T rows 2j, 2j+1 at k = 2 c4 .. 2 c4 + 7 from A_{K,:}[c4 .. c4+3][j]
+      const int j = base + (e & 127), c4 = 4 * (e >> 7);
+      const bool in = (j >= k0 && j < k0 + W);
+      uint32_t h0[4], h1[4], l0[4], l1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 z = in ? make_float2(j - k0 == c4 + q ? 1.f : 0.f, 0.f) : src[(size_t)(k0 + c4 + q) * np + j];
+        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        split2(z.x, rh, rl);
+        split2(z.y, ih, il);
+        split2(-z.y, nh, nl);
+        h0[q] = bf2_bits(rh, nh);
+        h1[q] = bf2_bits(ih, rh);
+        l0[q] = bf2_bits(rl, nl);
+        l1[q] = bf2_bits(il, rl);
+      }
+      const size_t o0 = img_offset(2 * j, 2 * c4, kKtW), o1 = img_offset(2 * j + 1, 2 * c4, kKtW);
+      *reinterpret_cast<uint4*>(td + o0) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+      *reinterpret_cast<uint4*>(td + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+      *reinterpret_cast<uint4*>(td + tslice + o0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
+      *reinterpret_cast<uint4*>(td + tslice + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
     }
   }
 }
@@ -898,7 +1039,13 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
     __nv_bfloat16* nxt_c = cimg + ((step + 1) & 1) * chalf;
     __nv_bfloat16* nxt_t = timg + ((step + 1) & 1) * thalf;
     if constexpr (W == 128) {
-      gj_pivot_pack_kernel<<<nb, 1024, 0, st>>>(A, np, k0, pimg, pstride, pslice, status);
+      static bool attr = false;
+      if (!attr) {
+        NED_CUDA(cudaFuncSetAttribute(gj_pivot_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kPivSmem));
+        attr = true;
+      }
+      gj_pivot_pack_kernel<<<nb, 1024, kPivSmem, st>>>(A, np, k0, pimg, pstride, pslice, status);
       NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
     } else {
       // P = inv(A_KK): the W = 128 Gauss-Jordan on copies of the diagonal blocks
@@ -1113,38 +1260,56 @@ __global__ void oz_coef_kernel(ContourDev c, ModelDev m, const double* __restric
 
 // A'_b = P (B_q - S) in FP32 from the shared base -S (np x np, identity
 // padding): row r copies base row i = sigma(r) and adds the three entries of
-// B_q in row i.  One block per (row, matrix).
-__global__ void __launch_bounds__(128) gen_a_fast_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
+// B_q in row i.  Block (x, y): rows 32x .. 32x+31 of matrix y; lane r of warp
+// 0 forms the B_q entries of row 32x + r (FP64), then warp w copies rows
+// w, w + 8, ... with 16-byte loads and stores.
+constexpr int kGenRows = 32;
+__global__ void __launch_bounds__(256) gen_a_fast_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
                                                          const double* __restrict__ ebar_d, int q0,
                                                          const float2* __restrict__ base, float2* __restrict__ A,
                                                          int np) {
-  const int r = blockIdx.x, b = blockIdx.y;
-  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
-  __shared__ float2 bv[3];
-  __shared__ int bc[3];
-  int i = r;
-  if (r < c.n && shifted_point(m, eps)) i = (r + 1 == c.n) ? 0 : r + 1;
-  if (threadIdx.x == 0) {
-    bc[0] = bc[1] = bc[2] = -1;
+  const int r0 = blockIdx.x * kGenRows, b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ float2 bv[kGenRows][3];
+  __shared__ int bc[kGenRows][3];
+  __shared__ int src_row[kGenRows];
+  if (warp == 0) {
+    const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
+    const int r = r0 + lane;
+    int i = r;
+    if (r < c.n && shifted_point(m, eps)) i = (r + 1 == c.n) ? 0 : r + 1;
+    src_row[lane] = i;
+    bc[lane][0] = bc[lane][1] = bc[lane][2] = -1;
     if (i < c.n) {
-      bc[0] = i;
-      bv[0] = make_float2(0.f, 1.f);
-      if (i >= 1) { const double2 z = b_sub(c, m, eps, ebar, i); bc[1] = i - 1; bv[1] = make_float2((float)z.x, (float)z.y); }
-      if (i == 0 && c.n > 1) { const double2 z = b_corner(c, m, eps); bc[2] = c.n - 1; bv[2] = make_float2((float)z.x, (float)z.y); }
+      bc[lane][0] = i;
+      bv[lane][0] = make_float2(0.f, 1.f);
+      if (i >= 1) {
+        const double2 z = b_sub(c, m, eps, ebar, i);
+        bc[lane][1] = i - 1;
+        bv[lane][1] = make_float2((float)z.x, (float)z.y);
+      }
+      if (i == 0 && c.n > 1) {
+        const double2 z = b_corner(c, m, eps);
+        bc[lane][2] = c.n - 1;
+        bv[lane][2] = make_float2((float)z.x, (float)z.y);
+      }
     }
   }
   __syncthreads();
-  const float4* src = reinterpret_cast<const float4*>(base + (size_t)i * np);
-  float4* dst = reinterpret_cast<float4*>(A + (size_t)b * np * np + (size_t)r * np);
-  for (int v = threadIdx.x; v < np / 2; v += blockDim.x) {
-    float4 x = src[v];
-    const int ja = 2 * v, jb = 2 * v + 1;
+  for (int rr = warp; rr < kGenRows; rr += 8) {
+    const int r = r0 + rr;
+    const float4* src = reinterpret_cast<const float4*>(base + (size_t)src_row[rr] * np);
+    float4* dst = reinterpret_cast<float4*>(A + (size_t)b * np * np + (size_t)r * np);
+    for (int v = lane; v < np / 2; v += 32) {
+      float4 x = src[v];
+      const int ja = 2 * v, jb = 2 * v + 1;
 #pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      if (bc[e] == ja) { x.x += bv[e].x; x.y += bv[e].y; }
-      if (bc[e] == jb) { x.z += bv[e].x; x.w += bv[e].y; }
+      for (int e = 0; e < 3; ++e) {
+        if (bc[rr][e] == ja) { x.x += bv[rr][e].x; x.y += bv[rr][e].y; }
+        if (bc[rr][e] == jb) { x.z += bv[rr][e].x; x.w += bv[rr][e].y; }
+      }
+      dst[v] = x;
     }
-    dst[v] = x;
   }
 }
 
@@ -1603,7 +1768,7 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
   const size_t mat = (size_t)np * np;
   const size_t xs = (size_t)2 * np * 2 * np, as = (size_t)np * 2 * np, rs = (size_t)2 * np * 2 * np;
   int rc;
-  gen_a_fast_kernel<<<dim3(np, nb), 128, 0, st>>>(c, m, eps, ebar, q0, sh.base, X, np);
+  gen_a_fast_kernel<<<dim3(np / kGenRows, nb), 256, 0, st>>>(c, m, eps, ebar, q0, sh.base, X, np);
   NED_LAUNCH_CHECK("gen_a_fast_kernel");
   if ((rc = gj_blocked_umma(X, c.n, np, nb, scratch, status, st))) return rc;
   oz_coef_kernel<<<dim3((np + 255) / 256, nb), 256, 0, st>>>(c, m, eps, ebar, q0, S, np, coef, sh.flags);
