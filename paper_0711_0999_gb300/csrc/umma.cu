@@ -41,6 +41,19 @@ struct GemmParams {
   int* status;
 };
 
+// The persistent kernel loads its operands in half tiles (128 rows x 32 k,
+// 8 KB) through one tensor map over a buffer of packed images: 4-D, (element
+// of a core-matrix row, core column of the tile, 8-row group, tile), the tile
+// index counting 16 KB from the map's base.  Every operand starts at a tile
+// boundary; a / b give tile indices of batch entry 0, slice 0.
+struct TileMapParams {
+  CUtensorMap map;
+  long long a, a_batch, a_slice;  // tiles
+  long long b, b_batch, b_slice;
+  int kt;                          // K tiles (64 k) of the product
+  int* status;
+};
+
 template <int BN, int SA, int SB, int STAGES>
 struct Cfg {
   static constexpr int kBn = BN;
@@ -198,11 +211,60 @@ int launch_gemm(const GemmParams& p, int n_tiles, int m_tiles, int batch, const 
 
 using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (192 KB)
 
+// Stages of half tiles (32 k): 4 x 48 KB for the persistent Gauss-Jordan products.
+template <int BN, int SA, int SB, int STAGES>
+struct CfgHalf {
+  static constexpr int kBn = BN;
+  static constexpr int kSa = SA;
+  static constexpr int kSb = SB;
+  static constexpr int kStages = STAGES;
+  static constexpr int kBTiles = BN / kTileRows;
+  static constexpr int kHalfBytes = kTileBytes / 2;
+  static constexpr int kStageBytes = (SA + SB * kBTiles) * kHalfBytes;
+  static constexpr int kSmem = STAGES * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+};
+using CfgGJH = CfgHalf<256, 2, 2, 4>;
+
 // Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear order
 // (batch, m tile, n tile), n fastest.  The stage ring runs on across tiles and
 // the TMEM holds two accumulators, so the epilogue of one tile overlaps the
 // loads and products of the next.  Epi::prefetch(b, mt, nt) may warm L2 for
 // the epilogue's own reads.
+// The tiles of one CTA of a persistent launch, t = c, c + G, ... < total,
+// visited so that the ones with a slow epilogue (Epi::heavy) are spread evenly
+// among the rest (the epilogue may lag the products by one accumulator
+// only).  Every role of the CTA walks the same sequence.
+template <class Epi>
+struct TileSeq {
+  int c, G, total, per, n_tiles, n, nh, i, taken_h, next_h, next_l;
+  __device__ bool heavy(const Epi& e, int t) const {
+    const int rem = t % per;
+    return e.heavy(rem / n_tiles, rem % n_tiles);
+  }
+  __device__ int advance(const Epi& e, int t, bool want_heavy) const {
+    while (t < total && heavy(e, t) != want_heavy) t += G;
+    return t;
+  }
+  __device__ void init(const Epi& e, int c_, int G_, int total_, int per_, int n_tiles_) {
+    c = c_; G = G_; total = total_; per = per_; n_tiles = n_tiles_;
+    n = 0; nh = 0;
+    for (int t = c; t < total; t += G) { ++n; nh += heavy(e, t) ? 1 : 0; }
+    i = 0; taken_h = 0;
+    next_h = advance(e, c, true);
+    next_l = advance(e, c, false);
+  }
+  // the next tile, or -1 at the end
+  __device__ int next(const Epi& e) {
+    if (i >= n) return -1;
+    const bool take_h = (long long)(i + 1) * nh / n > taken_h;
+    int t;
+    if (take_h) { t = next_h; next_h = advance(e, next_h + G, true); ++taken_h; }
+    else { t = next_l; next_l = advance(e, next_l + G, false); }
+    ++i;
+    return t;
+  }
+};
+
 // Epilogues with Epi::kStage stage -acc of plain tiles in shared memory, one
 // 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, kRedBuf
 // boxes per warp, and add it into the output at L2 with one tensor bulk
@@ -214,7 +276,8 @@ constexpr int red_stage_bytes() { return 768 + EPIW * kRedBuf * kRedBox; }
 
 template <class C, class Pairs, class Epi, int EPIW>
 __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
-    umma_gemm_persistent_kernel(GemmParams p, const __grid_constant__ Epi epi, int n_tiles, int m_tiles, int batch) {
+    umma_gemm_persistent_kernel(const __grid_constant__ TileMapParams p, const __grid_constant__ Epi epi, int n_tiles,
+                                int m_tiles, int batch) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
@@ -254,26 +317,27 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < total && ok; t += G) {
+      TileSeq<Epi> seq;
+      seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+      for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi)) {
         const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
         const int mt = rem / n_tiles, nt = rem % n_tiles;
         epi.prefetch(b, mt, nt);
-        const __nv_bfloat16* a = p.a + b * p.a_batch;
-        const __nv_bfloat16* bb = p.b + b * p.b_batch;
-        for (int kt = 0; kt < p.kt; ++kt, ++it) {
+        const long long a0 = p.a + b * p.a_batch + (long long)mt * p.kt;
+        const long long b0 = p.b + b * p.b_batch + (long long)nt * C::kBTiles * p.kt;
+        for (int h = 0; h < 2 * p.kt; ++h, ++it) {  // half tiles: kt = h / 2, core columns 4 (h % 2) .. +3
           const int s = it % C::kStages;
           const uint32_t ph = (it / C::kStages) & 1;
           if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) { ok = false; break; }
           unsigned char* st = smem + s * C::kStageBytes;
+          const int kt = h >> 1, kc = 4 * (h & 1);
           mbar_arrive_expect_tx(&full[s], C::kStageBytes);
           for (int sa = 0; sa < C::kSa; ++sa)
-            bulk_g2s(st + sa * kTileBytes, a + sa * p.a_slice + ((size_t)mt * p.kt + kt) * kTileElems, kTileBytes,
-                     &full[s]);
+            tma_load_4d(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), &full[s]);
           for (int sb = 0; sb < C::kSb; ++sb)
             for (int u = 0; u < C::kBTiles; ++u)
-              bulk_g2s(st + (C::kSa + sb * C::kBTiles + u) * kTileBytes,
-                       bb + sb * p.b_slice + ((size_t)(nt * C::kBTiles + u) * p.kt + kt) * kTileElems, kTileBytes,
-                       &full[s]);
+              tma_load_4d(&p.map, st + (C::kSa + sb * C::kBTiles + u) * C::kHalfBytes, 0, kc, 0,
+                          (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt), &full[s]);
         }
       }
       // no copy may be left in flight at exit
@@ -288,26 +352,29 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
       int it = 0, lt = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < total && ok; t += G, ++lt) {
+      TileSeq<Epi> seq;
+      seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+      for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
         const int buf = lt & 1;
         if (lt >= 2) {
           if (!mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
         }
         const uint32_t d = tmem + buf * C::kBn;
-        for (int kt = 0; kt < p.kt; ++kt, ++it) {
+        for (int h = 0; h < 2 * p.kt; ++h, ++it) {
           const int s = it % C::kStages;
           if (!mbar_wait(&full[s], (it / C::kStages) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+          // half tile: 4 core columns (LBO 128 B), 8-row groups 512 B apart
 #pragma unroll
-          for (int kk = 0; kk < kTileK / 16; ++kk) {
+          for (int kk = 0; kk < kTileK / 32; ++kk) {
 #pragma unroll
             for (int q = 0; q < Pairs::kPairs; ++q) {
-              const uint32_t a_addr = st + Pairs::a(q) * kTileBytes + kk * 256;
-              const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * C::kBTiles) * kTileBytes + kk * 256;
-              mma_bf16(d, smem_desc(a_addr, 128, 1024), smem_desc(b_addr, 128, 1024), idesc,
-                       (kt > 0 || kk > 0 || q > 0) ? 1u : 0u);
+              const uint32_t a_addr = st + Pairs::a(q) * C::kHalfBytes + kk * 256;
+              const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * C::kBTiles) * C::kHalfBytes + kk * 256;
+              mma_bf16(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc,
+                       (h > 0 || kk > 0 || q > 0) ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
@@ -331,7 +398,9 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     int nred = 0;
     int lt = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += G, ++lt) {
+    TileSeq<Epi> seq;
+    seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+    for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
       const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
       const int mt = rem / n_tiles, nt = rem % n_tiles;
       const int buf = lt & 1;
@@ -363,6 +432,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
         if constexpr (Epi::kStage) {
           const int k = md == 2 ? ((c0 - c_begin) >> 5) & 1 : nred % kRedBuf;
+          const bool keep = md == 2 && epi.keeps(mt, nt);
           unsigned char* box = red_stage + k * kRedBox;
           if (md == 2) {
             if (c0 + 32 < c_end) load_box(k ^ 1, c0 + 32);
@@ -377,8 +447,10 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
             for (int u = 0; u < 8; ++u) o[u] = *reinterpret_cast<const float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4));
             epi.finish(b, mt, nt, row, c0, o, v);  // o: old -> new values; panels written
             __syncwarp();
+            if (keep)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) *reinterpret_cast<float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4)) = o[u];
+              for (int u = 0; u < 8; ++u)
+                *reinterpret_cast<float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4)) = o[u];
             nred = k + 1;  // the next plain box is the other one
           } else {
             // -acc of the warp's 32 rows x 32 columns as one swizzled box
@@ -396,7 +468,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
           // values are dropped or already applied)
           fence_proxy_async();
           __syncwarp();
-          if (lane == 0) {
+          if (lane == 0 && (md != 2 || keep)) {
             if (md == 0)
               tma_reduce_add_2d(&epi.red_map, box, epi.red_x(nt, c0), epi.red_y(b, mt, q * 32));
             else
@@ -428,7 +500,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
 }
 
 template <class C, class Pairs, int EPIW, class Epi>
-int launch_gemm_persistent(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
+int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi,
+                           cudaStream_t st) {
   const int smem_bytes = C::kSmem + (Epi::kStage ? red_stage_bytes<EPIW>() : 0);
   static bool attr = false;
   if (!attr) {
@@ -498,6 +571,13 @@ struct EpiUpdate {
     if (kn >= 0 && (in_block(nt * (CfgGJ::kBn / 2), kn) || in_block(mt * kTileRows, kn))) return 2;
     if (in_block(nt * (CfgGJ::kBn / 2), k0) || in_block(mt * kTileRows, k0)) return 1;
     return 0;
+  }
+  __device__ bool heavy(int mt, int nt) const { return mode(mt, nt) == 2; }
+  // Mode 2 tiles are stored back only in the diagonal block (Kn, Kn), which
+  // the next pivot reads; the rest of block row and column Kn is read only
+  // through the panels written here (the next update replaces it).
+  __device__ bool keeps(int mt, int nt) const {
+    return in_block(nt * (CfgGJ::kBn / 2), kn) && in_block(mt * kTileRows, kn);
   }
   // A of the whole batch as one FP32 tensor of 2 np columns and batch * np
   // rows: red_map boxes 32 x 32 with 128-byte swizzle (the staged -acc),
@@ -602,6 +682,7 @@ struct EpiRPack {
   static constexpr bool kStage = false;
   static constexpr int kKtW = 2 * W / kTileK;
   __device__ int mode(int, int) const { return 1; }
+  __device__ bool heavy(int, int) const { return false; }
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 W)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
@@ -932,14 +1013,16 @@ struct GjBuffers {
 };
 
 size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
+// the packed panels start at 16 KB boundaries (tile units of the operand tensor map)
+size_t align16k(size_t x) { return (x + 16383) & ~(size_t)16383; }
 
 template <int W>
 GjBuffers gj_buffers(int np) {
   GjBuffers g{};
-  g.mat = align1k(sizeof(float2) * (size_t)np * np);
-  g.pimg = align1k(2 * sizeof(__nv_bfloat16) * (size_t)W * 2 * W);
-  g.cimg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);
-  g.timg = 2 * align1k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * W);
+  g.mat = align16k(sizeof(float2) * (size_t)np * np);
+  g.pimg = align16k(2 * sizeof(__nv_bfloat16) * (size_t)W * 2 * W);
+  g.cimg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);
+  g.timg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * W);
   g.rimg = g.timg / 2;
   if constexpr (W > 128) {
     const GjBuffers in = gj_buffers<128>(W);
@@ -1001,6 +1084,22 @@ int encode_f32_rows(CUtensorMap* map, float* base, uint64_t cols, uint64_t rows,
 
 namespace {
 
+// 4-D tensor map over `tiles` packed 128 x 64 bf16 tiles (16 KB each) at
+// `base`, moved in half tiles: box (64 elements, 4 core columns, 16 row groups, 1).
+int encode_tile_map(CUtensorMap* map, void* base, uint64_t tiles) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[4] = {64, 8, 16, tiles};
+  const cuuint64_t strides[3] = {128, 1024, 16384};
+  const cuuint32_t box[4] = {64, 4, 16, 1};
+  const cuuint32_t elem_strides[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, elem_strides,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled (tiles) failed (CUresult %d)", (int)r);
+  return NEDMFT_OK;
+}
+
 template <int W>
 int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st,
                       bool instrument) {
@@ -1022,14 +1121,21 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
   const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
   // A of the whole batch as one tensor of 2 np FP32 columns and nb np rows,
   // for the update's staged bulk reductions and its L2 prefetch
-  CUtensorMap red_map, pre_map;
+  CUtensorMap red_map, pre_map, tile_map;
   {
     float* a = reinterpret_cast<float*>(A);
     const uint64_t cols = 2 * (uint64_t)np, rows = (uint64_t)nb * np;
     int rc = encode_f32_rows(&red_map, a, cols, rows, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = encode_f32_rows(&pre_map, a, cols, rows, CfgGJ::kBn, kTileRows, CU_TENSOR_MAP_SWIZZLE_NONE);
+    // the panels of the batch as packed tiles, for the products' operand loads
+    if (!rc) rc = encode_tile_map(&tile_map, scratch, per * nb / kTileBytes);
     if (rc) return rc;
   }
+  // tile index (16 KB units from scratch) of an image pointer
+  auto tile_of = [&](const __nv_bfloat16* ptr) {
+    return (long long)((reinterpret_cast<const char*>(ptr) - scratch) / kTileBytes);
+  };
+  const long long per_t = (long long)(per / kTileBytes);
   gj_panel_pack_kernel<W>
       <<<dim3(np / 128, nb), 256, 0, st>>>(A, np, 0, cimg, pstride, cslice, timg, pstride, tslice);
   NED_LAUNCH_CHECK("gj_panel_pack_kernel");
@@ -1060,20 +1166,22 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
       NED_LAUNCH_CHECK("gj_ppack_kernel");
     }
     {  // R = P A_{K,:}, W x 2np, K = 2W
-      GemmParams p{pimg, pstride, pslice, cur_t, pstride, tslice, kKtW, status};
+      TileMapParams p{tile_map, tile_of(pimg), per_t, (long long)(pslice / kTileElems),
+                      tile_of(cur_t), per_t, (long long)(tslice / kTileElems), kKtW, status};
       EpiRPack<W> epi{rimg, pstride, tslice};
-      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, W / kTileRows, nb, epi, st);
+      int rc = launch_gemm_persistent<CfgGJH, Split3, 4>(p, 2 * np / CfgGJ::kBn, W / kTileRows, nb, epi, st);
       if (rc) return rc;
     }
     {  // A <- A - C' R, np x 2np, K = 2W; next step's panels from the epilogue
-      GemmParams p{cur_c, pstride, cslice, rimg, pstride, tslice, kKtW, status};
+      TileMapParams p{tile_map, tile_of(cur_c), per_t, (long long)(cslice / kTileElems),
+                      tile_of(rimg), per_t, (long long)(tslice / kTileElems), kKtW, status};
       const int kn = (k0 + W < np) ? k0 + W : -1;
       EpiUpdate<W> epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
                        tslice};
       epi.red_map = red_map;
       epi.pre_map = pre_map;
       const int slot = instrument ? instr_begin(st) : -1;
-      int rc = launch_gemm_persistent<CfgGJ, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
+      int rc = launch_gemm_persistent<CfgGJH, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
       if (instrument) {
         const int live = n - k0 < W ? (n - k0 > 0 ? n - k0 : 0) : W;
