@@ -234,12 +234,16 @@ using CfgGJH = CfgHalf<256, 2, 2, 4>;
 // visited so that the ones with a slow epilogue (Epi::heavy) are spread evenly
 // among the rest (the epilogue may lag the products by one accumulator
 // only).  Every role of the CTA walks the same sequence.
-template <class Epi>
+template <class Epi, int PAIR>
 struct TileSeq {
   int c, G, total, per, n_tiles, n, nh, i, taken_h, next_h, next_l;
+  // unit t of `per` per batch entry: m-tile pair rem / n_tiles, n-tile rem % n_tiles
   __device__ bool heavy(const Epi& e, int t) const {
     const int rem = t % per;
-    return e.heavy(rem / n_tiles, rem % n_tiles);
+    bool h = false;
+#pragma unroll
+    for (int r = 0; r < PAIR; ++r) h = h || e.heavy(PAIR * (rem / n_tiles) + r, rem % n_tiles);
+    return h;
   }
   __device__ int advance(const Epi& e, int t, bool want_heavy) const {
     while (t < total && heavy(e, t) != want_heavy) t += G;
@@ -274,7 +278,10 @@ constexpr int kRedBox = 32 * 32 * 4;
 template <int EPIW>
 constexpr int red_stage_bytes() { return 768 + EPIW * kRedBuf * kRedBox; }
 
-template <class C, class Pairs, class Epi, int EPIW>
+// PAIR = 2: clusters of two CTAs take m tiles 2j and 2j+1 of the same n tile;
+// each loads its own A and half of B, multicast to both, and a stage is
+// refilled only when both CTAs' products have released it.
+template <class C, class Pairs, class Epi, int EPIW, int PAIR>
 __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     umma_gemm_persistent_kernel(const __grid_constant__ TileMapParams p, const __grid_constant__ Epi epi, int n_tiles,
                                 int m_tiles, int batch) {
@@ -287,14 +294,19 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = n_tiles * m_tiles * batch;
-  const int G = gridDim.x;
+  // work units: (batch entry, pair of m tiles, n tile) for PAIR = 2
+  const int per_u = n_tiles * (m_tiles / PAIR);
+  const int total = per_u * batch;
+  const int G = gridDim.x / PAIR;
+  const int cta = blockIdx.x / PAIR;
+  const int rank = PAIR == 2 ? (int)cluster_ctarank() : 0;
+  constexpr uint16_t kBoth = 3;
   constexpr uint32_t kCols = 2 * C::kBn;  // two accumulators
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], PAIR);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
@@ -310,6 +322,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
   if (warp == 1) tmem_alloc(tmem_slot, kCols);
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -317,11 +330,11 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      TileSeq<Epi> seq;
-      seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+      TileSeq<Epi, PAIR> seq;
+      seq.init(epi, cta, G, total, per_u, n_tiles);
       for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi)) {
-        const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
-        const int mt = rem / n_tiles, nt = rem % n_tiles;
+        const int b = t / per_u, rem = t % per_u;
+        const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
         epi.prefetch(b, mt, nt);
         const long long a0 = p.a + b * p.a_batch + (long long)mt * p.kt;
         const long long b0 = p.b + b * p.b_batch + (long long)nt * C::kBTiles * p.kt;
@@ -335,9 +348,16 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
           for (int sa = 0; sa < C::kSa; ++sa)
             tma_load_4d(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), &full[s]);
           for (int sb = 0; sb < C::kSb; ++sb)
-            for (int u = 0; u < C::kBTiles; ++u)
-              tma_load_4d(&p.map, st + (C::kSa + sb * C::kBTiles + u) * C::kHalfBytes, 0, kc, 0,
-                          (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt), &full[s]);
+            for (int u = 0; u < C::kBTiles; ++u) {
+              const int idx = sb * C::kBTiles + u;
+              unsigned char* dst = st + (C::kSa + idx) * C::kHalfBytes;
+              const int L = (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt);
+              if constexpr (PAIR == 2) {
+                if ((idx & 1) == rank) tma_load_4d_mc(&p.map, dst, 0, kc, 0, L, &full[s], kBoth);
+              } else {
+                tma_load_4d(&p.map, dst, 0, kc, 0, L, &full[s]);
+              }
+            }
         }
       }
       // no copy may be left in flight at exit
@@ -352,8 +372,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
       int it = 0, lt = 0;
       bool ok = true;
-      TileSeq<Epi> seq;
-      seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+      TileSeq<Epi, PAIR> seq;
+      seq.init(epi, cta, G, total, per_u, n_tiles);
       for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
         const int buf = lt & 1;
         if (lt >= 2) {
@@ -377,7 +397,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
                        (h > 0 || kk > 0 || q > 0) ? 1u : 0u);
             }
           }
-          mma_commit(&empty[s]);
+          if constexpr (PAIR == 2) mma_commit_mc(&empty[s], kBoth);
+          else mma_commit(&empty[s]);
         }
         mma_commit(&acc_full[buf]);
       }
@@ -398,11 +419,11 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     int nred = 0;
     int lt = 0;
     bool ok = true;
-    TileSeq<Epi> seq;
-    seq.init(epi, blockIdx.x, G, total, n_tiles * m_tiles, n_tiles);
+    TileSeq<Epi, PAIR> seq;
+    seq.init(epi, cta, G, total, per_u, n_tiles);
     for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
-      const int b = t / (n_tiles * m_tiles), rem = t % (n_tiles * m_tiles);
-      const int mt = rem / n_tiles, nt = rem % n_tiles;
+      const int b = t / per_u, rem = t % per_u;
+      const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
       const int buf = lt & 1;
       const int md = epi.mode(mt, nt);
       const int row = q * 32 + lane;
@@ -492,6 +513,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     if (Epi::kStage) bulk_wait_all();
   }
   __syncthreads();
+  if constexpr (PAIR == 2) cluster_sync();  // no multicast into a CTA that has left
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, kCols);
@@ -503,11 +525,39 @@ template <class C, class Pairs, int EPIW, class Epi>
 int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi,
                            cudaStream_t st) {
   const int smem_bytes = C::kSmem + (Epi::kStage ? red_stage_bytes<EPIW>() : 0);
-  static bool attr = false;
-  if (!attr) {
-    NED_CUDA(cudaFuncSetAttribute(umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
-    attr = true;
+  const dim3 block(64 + 32 * EPIW);
+  if (m_tiles % 2 == 0) {
+    // clusters of two CTAs sharing B; as many clusters as fit at once
+    auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 2>;
+    static int max_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (!max_clusters) {
+      NED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+      cfg.gridDim = dim3(2);
+      NED_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
+      if (max_clusters < 1) return set_error(NEDMFT_ECUDA, "persistent GEMM: no cluster of 2 fits on this device");
+    }
+    const int units = n_tiles * (m_tiles / 2) * batch;
+    cfg.gridDim = dim3(2 * (units < max_clusters ? units : max_clusters));
+    NED_CUDA(cudaLaunchKernelEx(&cfg, kern, p, epi, n_tiles, m_tiles, batch));
+    NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
+    return NEDMFT_OK;
+  }
+  auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 1>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    NED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+    attr_set = true;
   }
   static int sms = 0;
   if (!sms) {
@@ -517,8 +567,7 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
   }
   const int total = n_tiles * m_tiles * batch;
   const int grid = total < sms ? total : sms;
-  umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>
-      <<<grid, 64 + 32 * EPIW, smem_bytes, st>>>(p, epi, n_tiles, m_tiles, batch);
+  kern<<<grid, block, smem_bytes, st>>>(p, epi, n_tiles, m_tiles, batch);
   NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
   return NEDMFT_OK;
 }
