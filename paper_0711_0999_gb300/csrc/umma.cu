@@ -225,50 +225,12 @@ struct CfgHalf {
 };
 using CfgGJH = CfgHalf<256, 2, 2, 4>;
 
-// Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear order
-// (batch, m tile, n tile), n fastest.  The stage ring runs on across tiles and
-// the TMEM holds two accumulators, so the epilogue of one tile overlaps the
-// loads and products of the next.  Epi::prefetch(b, mt, nt) may warm L2 for
-// the epilogue's own reads.
-// The tiles of one CTA of a persistent launch, t = c, c + G, ... < total,
-// visited so that the ones with a slow epilogue (Epi::heavy) are spread evenly
-// among the rest (the epilogue may lag the products by one accumulator
-// only).  Every role of the CTA walks the same sequence.
-template <class Epi, int PAIR>
-struct TileSeq {
-  int c, G, total, per, n_tiles, n, nh, i, taken_h, next_h, next_l;
-  // unit t of `per` per batch entry: m-tile pair rem / n_tiles, n-tile rem % n_tiles
-  __device__ bool heavy(const Epi& e, int t) const {
-    const int rem = t % per;
-    bool h = false;
-#pragma unroll
-    for (int r = 0; r < PAIR; ++r) h = h || e.heavy(PAIR * (rem / n_tiles) + r, rem % n_tiles);
-    return h;
-  }
-  __device__ int advance(const Epi& e, int t, bool want_heavy) const {
-    while (t < total && heavy(e, t) != want_heavy) t += G;
-    return t;
-  }
-  __device__ void init(const Epi& e, int c_, int G_, int total_, int per_, int n_tiles_) {
-    c = c_; G = G_; total = total_; per = per_; n_tiles = n_tiles_;
-    n = 0; nh = 0;
-    for (int t = c; t < total; t += G) { ++n; nh += heavy(e, t) ? 1 : 0; }
-    i = 0; taken_h = 0;
-    next_h = advance(e, c, true);
-    next_l = advance(e, c, false);
-  }
-  // the next tile, or -1 at the end
-  __device__ int next(const Epi& e) {
-    if (i >= n) return -1;
-    const bool take_h = (long long)(i + 1) * nh / n > taken_h;
-    int t;
-    if (take_h) { t = next_h; next_h = advance(e, next_h + G, true); ++taken_h; }
-    else { t = next_l; next_l = advance(e, next_l + G, false); }
-    ++i;
-    return t;
-  }
-};
-
+// Persistent form: CTA (or CTA pair) c takes tiles c, c + G, c + 2G, ... of
+// the linear order (batch, m tile, n tile), n fastest, so that at any time the
+// CTAs work on about one matrix and its operand panels stay in L2.  The stage
+// ring runs on across tiles and the TMEM holds two accumulators, so the
+// epilogue of one tile overlaps the loads and products of the next.
+//
 // Epilogues with Epi::kStage stage -acc of plain tiles in shared memory, one
 // 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, kRedBuf
 // boxes per warp, and add it into the output at L2 with one tensor bulk
@@ -330,12 +292,9 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      TileSeq<Epi, PAIR> seq;
-      seq.init(epi, cta, G, total, per_u, n_tiles);
-      for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi)) {
+      for (int t = cta; t < total && ok; t += G) {
         const int b = t / per_u, rem = t % per_u;
         const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
-        epi.prefetch(b, mt, nt);
         const long long a0 = p.a + b * p.a_batch + (long long)mt * p.kt;
         const long long b0 = p.b + b * p.b_batch + (long long)nt * C::kBTiles * p.kt;
         for (int h = 0; h < 2 * p.kt; ++h, ++it) {  // half tiles: kt = h / 2, core columns 4 (h % 2) .. +3
@@ -372,9 +331,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
       int it = 0, lt = 0;
       bool ok = true;
-      TileSeq<Epi, PAIR> seq;
-      seq.init(epi, cta, G, total, per_u, n_tiles);
-      for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
+      for (int t = cta; t < total && ok; t += G, ++lt) {
         const int buf = lt & 1;
         if (lt >= 2) {
           if (!mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
@@ -419,9 +376,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     int nred = 0;
     int lt = 0;
     bool ok = true;
-    TileSeq<Epi, PAIR> seq;
-    seq.init(epi, cta, G, total, per_u, n_tiles);
-    for (int t = seq.next(epi); t >= 0 && ok; t = seq.next(epi), ++lt) {
+    for (int t = cta; t < total && ok; t += G, ++lt) {
       const int b = t / per_u, rem = t % per_u;
       const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
       const int buf = lt & 1;
@@ -621,7 +576,6 @@ struct EpiUpdate {
     if (in_block(nt * (CfgGJ::kBn / 2), k0) || in_block(mt * kTileRows, k0)) return 1;
     return 0;
   }
-  __device__ bool heavy(int mt, int nt) const { return mode(mt, nt) == 2; }
   // Mode 2 tiles are stored back only in the diagonal block (Kn, Kn), which
   // the next pivot reads; the rest of block row and column Kn is read only
   // through the panels written here (the next update replaces it).
@@ -629,16 +583,10 @@ struct EpiUpdate {
     return in_block(nt * (CfgGJ::kBn / 2), kn) && in_block(mt * kTileRows, kn);
   }
   // A of the whole batch as one FP32 tensor of 2 np columns and batch * np
-  // rows: red_map boxes 32 x 32 with 128-byte swizzle (the staged -acc),
-  // pre_map boxes of one tile, 256 x 128, for the L2 prefetch
-  CUtensorMap red_map, pre_map;
+  // rows, moved in boxes of 32 x 32 with 128-byte swizzle (the staged -acc)
+  CUtensorMap red_map;
   __device__ int red_x(int nt, int c0) const { return nt * CfgGJ::kBn + c0; }
   __device__ int red_y(int b, int mt, int r0) const { return b * np + mt * kTileRows + r0; }
-  // warm L2 with the tile's old values
-  __device__ void prefetch(int b, int mt, int nt) const {
-    if (in_block(nt * (CfgGJ::kBn / 2), k0) || in_block(mt * kTileRows, k0)) return;  // old values unused
-    tma_prefetch_2d(&pre_map, nt * CfgGJ::kBn, b * np + mt * kTileRows);
-  }
   // mode 2 chunk of row r, real columns c0 .. c0+31 of the tile: o holds the
   // old values and gets the new ones, old - acc (old values in block K
   // dropped); the next step's panels are written from them
@@ -731,11 +679,9 @@ struct EpiRPack {
   static constexpr bool kStage = false;
   static constexpr int kKtW = 2 * W / kTileK;
   __device__ int mode(int, int) const { return 1; }
-  __device__ bool heavy(int, int) const { return false; }
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 W)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
-  __device__ void prefetch(int, int, int) const {}
   __device__ void operator()(int b, int mt, int nt, int r_tile, int c0, const float* v) const {
     __nv_bfloat16* base = img + b * bstride;
     const int r = mt * kTileRows + r_tile;  // row of R
@@ -1169,13 +1115,12 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
   // k & 1 while its update writes step k+1's panels into the other one
   const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
   // A of the whole batch as one tensor of 2 np FP32 columns and nb np rows,
-  // for the update's staged bulk reductions and its L2 prefetch
-  CUtensorMap red_map, pre_map, tile_map;
+  // for the update's staged bulk reductions and box loads
+  CUtensorMap red_map, tile_map;
   {
     float* a = reinterpret_cast<float*>(A);
     const uint64_t cols = 2 * (uint64_t)np, rows = (uint64_t)nb * np;
     int rc = encode_f32_rows(&red_map, a, cols, rows, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (!rc) rc = encode_f32_rows(&pre_map, a, cols, rows, CfgGJ::kBn, kTileRows, CU_TENSOR_MAP_SWIZZLE_NONE);
     // the panels of the batch as packed tiles, for the products' operand loads
     if (!rc) rc = encode_tile_map(&tile_map, scratch, per * nb / kTileBytes);
     if (rc) return rc;
@@ -1228,7 +1173,6 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
       EpiUpdate<W> epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
                        tslice};
       epi.red_map = red_map;
-      epi.pre_map = pre_map;
       const int slot = instrument ? instr_begin(st) : -1;
       int rc = launch_gemm_persistent<CfgGJH, Split3, 4>(p, 2 * np / CfgGJ::kBn, np / kTileRows, nb, epi, st);
       if (rc) return rc;
