@@ -165,17 +165,30 @@ def load_peaks():
         "fallback"
 
 
+# DRAM bytes of one Gauss-Jordan update launch (152 matrices at N_c = 1500), from
+# an ncu capture of the same kernel on 16 matrices scaled by 152 / 16; to be
+# re-taken whenever the update kernel changes
+UPDATE_TRAFFIC_BYTES = 715.6e6 * 152 / 16
+
+
 def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str, clocks):
     if precision == "mixed_bf16":
-        # arithmetic intensity of a rank-128 update: 8 N^2 128 flops per 2 N^2 8 B of
-        # FP32 complex traffic = 64 flop/B (192 issued bf16 flop/B), below the
-        # sustained bf16 / HBM balance (~263 flop/B): the kernel is HBM-bound
-        peak = peaks["hbm_gbs"]
-        tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                "traffic": None, "peak_source": f"HBM copy bandwidth, {src}",
-                "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
-                           "note": "algorithmic 8 N_c^2 nb flops per rank-nb step; 3 bf16 products issued per flop"}}
+        # a rank-W step of the Gauss-Jordan update (W = 256 complex columns at
+        # N_c = 1500) does 8 N^2 W flops per 2 N^2 8 B of FP32 complex traffic,
+        # W / 2 = 128 flop/B; in bf16x3 every flop is three bf16 products, so the
+        # tensor peak for this arithmetic is the bf16 peak / 3 and the balance
+        # point (sustained bf16 / 3 over HBM) is ~88 flop/B: the kernel is
+        # bound by the tensor cores
+        bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak = bf16 / 3.0
+        hpeak = peaks["hbm_gbs"]
+        return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                "traffic": UPDATE_TRAFFIC_BYTES,
+                "traffic_note": "ncu dram__bytes_read + write of one update launch on 16 matrices (715 MB), "
+                                "scaled by 152/16 to the benchmark launch",
+                "peak_source": f"sustained bf16 tensor rate / 3 (bf16x3 = three bf16 products per flop), {src}",
+                "hbm": {"achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
+                        "note": "algorithmic read + write of the FP32 complex matrix per step"}}
     mhz = peaks.get("sm_max_mhz", 2070.0)
     if precision == "mixed_fp32":
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock

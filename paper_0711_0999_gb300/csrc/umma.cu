@@ -1215,6 +1215,7 @@ constexpr int kOzBits = 7;        // bits per slice
 constexpr int kOzPairs = 10;      // slice pairs with a + b <= kOzS - 1
 constexpr int kOzBn = 64;         // output columns per tile (32 complex)
 constexpr int kOzChunkKt = 16;    // K tiles per exact chunk (1024)
+constexpr int kRedMaxBatch = 512;
 constexpr double kRefineTail = 1e-3;
 
 __device__ __forceinline__ void oz_pair(int q, int& a, int& b, int& d) {
@@ -1498,11 +1499,11 @@ __global__ void __launch_bounds__(256) oz_pack_x_kernel(const float2* __restrict
 }
 
 struct OzParams {
-  const __nv_bfloat16* a;  // S_d slices (shared)
-  size_t a_slice;
+  CUtensorMap a_map;       // S_d slices (shared), packed tiles from the first slice
+  CUtensorMap b_map;       // X' slices of the batch, packed tiles from matrix 0
+  long long a_slice;       // tiles between S_d slices
+  long long b_batch, b_slice;  // tiles between matrices / slices of X'
   const int* a_exp;        // row exponents
-  const __nv_bfloat16* b;  // X' slices per matrix
-  size_t b_batch, b_slice;
   const int* b_exp;        // column exponents per matrix (np each)
   const float2* X;         // X' per matrix (np x np)
   const float4* coef;      // per matrix (np x 3)
@@ -1512,20 +1513,22 @@ struct OzParams {
   ContourDev c;
   ModelDev m;
   const double* eps;
-  int q0, np, kt;
+  int q0, nb, np, kt;
   int* status;
 };
 
-constexpr int kOzStageBytes = kOzS * kTileBytes + kOzS * (kTileBytes / 2);  // 96 KB
-constexpr int kOzStages = 2;
+// Stages of half tiles (32 k): A kOzS x 8 KB, B (64 rows) kOzS x 4 KB.
+constexpr int kOzHalfA = kTileBytes / 2, kOzHalfB = kTileBytes / 4;
+constexpr int kOzStageBytes = kOzS * (kOzHalfA + kOzHalfB);  // 48 KB
+constexpr int kOzStages = 4;
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 
-// grid (m tiles, n tiles, batch): consecutive CTAs share the B tile.
-// TMEM: two buffers of kOzS accumulators of kOzBn columns (chunk c in buffer
-// c & 1), so the epilogue drains one chunk while the next one is multiplied.
-__global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
-  const int bidx = blockIdx.z;
-  if (!p.flags[p.q0 + bidx]) return;
+// Persistent: the units (refined matrix, m tile, n tile), m fastest, are
+// dealt round-robin to the CTAs; consecutive units share the B tile and all
+// share A (S_d), which stays in L2.  Chunks of kOzChunkKt K tiles alternate
+// between two TMEM buffers of kOzS accumulators of kOzBn columns across units,
+// so the epilogue drains (and finishes a unit) while the next chunk is multiplied.
+__global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
@@ -1534,9 +1537,14 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
   uint64_t* acc_empty = acc_full + 2;      // 2 buffers
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  __shared__ int refined[kRedMaxBatch];
+  __shared__ int n_refined;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y;
-  const int nchunks = (p.kt + kOzChunkKt - 1) / kOzChunkKt;
+  const int m_tiles = p.np / kTileRows, n_tiles = 2 * p.np / kOzBn;
+  const int per = m_tiles * n_tiles;
+  const int kh = 2 * p.kt;                  // half tiles per unit
+  const int hc = 2 * kOzChunkKt;            // half tiles per chunk
+  const int nchunks = (kh + hc - 1) / hc;   // chunks per unit
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kOzStages; ++s) {
@@ -1549,36 +1557,47 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
     }
     *abort_flag = 0;
     fence_barrier_init();
+    int r = 0;
+    for (int b = 0; b < p.nb; ++b)
+      if (p.flags[p.q0 + b]) refined[r++] = b;
+    n_refined = r;
   }
   if (warp == 1) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int units = n_refined * per;
+  const int G = gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
-      const __nv_bfloat16* b = p.b + bidx * p.b_batch;
-      int issued = 0;
-      for (int kt = 0; kt < p.kt; ++kt) {
-        const int s = kt % kOzStages;
-        const uint32_t ph = (kt / kOzStages) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) break;
-        unsigned char* st = smem + s * kOzStageBytes;
-        mbar_arrive_expect_tx(&full[s], kOzStageBytes);
-        for (int sl = 0; sl < kOzS; ++sl)
-          bulk_g2s(st + sl * kTileBytes, p.a + sl * p.a_slice + ((size_t)mt * p.kt + kt) * kTileElems, kTileBytes,
-                   &full[s]);
-        // B rows nt*64 .. +63: half (nt & 1) of image tile nt >> 1
-        for (int sl = 0; sl < kOzS; ++sl)
-          bulk_g2s(st + kOzS * kTileBytes + sl * (kTileBytes / 2),
-                   b + sl * p.b_slice + ((size_t)(nt >> 1) * p.kt + kt) * kTileElems + (nt & 1) * (kTileElems / 2),
-                   kTileBytes / 2, &full[s]);
-        issued = kt + 1;
+      int it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += G) {
+        const int bidx = refined[u / per], rem = u % per;
+        const int mt = rem % m_tiles, nt = rem / m_tiles;
+        const long long a0 = (long long)mt * p.kt;
+        const long long b0 = bidx * p.b_batch + (long long)(nt >> 1) * p.kt;
+        const int rg = 8 * (nt & 1);  // B rows nt*64 .. +63: row groups 8 (nt & 1) .. +7 of tile nt >> 1
+        for (int h = 0; h < kh; ++h, ++it) {
+          const int s = it % kOzStages;
+          const uint32_t ph = (it / kOzStages) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) { ok = false; break; }
+          unsigned char* st = smem + s * kOzStageBytes;
+          const int kt = h >> 1, kc = 4 * (h & 1);
+          mbar_arrive_expect_tx(&full[s], kOzStageBytes);
+          for (int sl = 0; sl < kOzS; ++sl)
+            tma_load_4d(&p.a_map, st + sl * kOzHalfA, 0, kc, 0, (int)(a0 + sl * p.a_slice + kt), &full[s]);
+          for (int sl = 0; sl < kOzS; ++sl)
+            tma_load_4d(&p.b_map, st + kOzS * kOzHalfA + sl * kOzHalfB, 0, kc, rg, (int)(b0 + sl * p.b_slice + kt),
+                        &full[s]);
+        }
       }
-      for (int kt = issued - kOzStages < 0 ? 0 : issued - kOzStages; kt < issued; ++kt) {
+      // no copy may be left in flight at exit
+      for (int k = it - kOzStages < 0 ? 0 : it - kOzStages; k < it; ++k) {
         const uint64_t t0 = global_ns();
-        while (!mbar_test(&full[kt % kOzStages], (kt / kOzStages) & 1) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_test(&full[k % kOzStages], (k / kOzStages) & 1) && global_ns() - t0 < kWaitNs) {
         }
       }
     }
@@ -1586,32 +1605,38 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(128, kOzBn);
       bool ok = true;
-      for (int kt = 0; kt < p.kt; ++kt) {
-        const int ch = kt / kOzChunkKt, buf = ch & 1;
-        const bool first = (kt % kOzChunkKt) == 0;
-        if (first && ch >= 2) {
-          if (!mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+      int it = 0, cg = 0;  // stage uses, chunks (across units)
+      for (int u = blockIdx.x; u < units && ok; u += G) {
+        for (int h = 0; h < kh && ok; ++h, ++it) {
+          const bool first = (h % hc) == 0;
+          const int buf = cg & 1;
+          if (first && cg >= 2) {
+            if (!mbar_wait(&acc_empty[buf], ((cg >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+          }
+          const int s = it % kOzStages;
+          if (!mbar_wait(&full[s], (it / kOzStages) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
-        }
-        const int s = kt % kOzStages;
-        if (!mbar_wait(&full[s], (kt / kOzStages) & 1, abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t st = smem_u32(smem + s * kOzStageBytes);
+          const uint32_t st = smem_u32(smem + s * kOzStageBytes);
 #pragma unroll
-        for (int kk = 0; kk < kTileK / 16; ++kk) {
+          for (int kk = 0; kk < kTileK / 32; ++kk) {
 #pragma unroll
-          for (int q = 0; q < kOzPairs; ++q) {
-            int a, b, d;
-            oz_pair(q, a, b, d);
-            const bool first_of_d = (q == 0 || q == 1 || q == 3 || q == 6);
-            const uint32_t a_addr = st + a * kTileBytes + kk * 256;
-            const uint32_t b_addr = st + kOzS * kTileBytes + b * (kTileBytes / 2) + kk * 256;
-            mma_bf16(tmem + buf * 256 + d * kOzBn, smem_desc(a_addr, 128, 1024), smem_desc(b_addr, 128, 1024), idesc,
-                     (first && kk == 0 && first_of_d) ? 0u : 1u);
+            for (int q = 0; q < kOzPairs; ++q) {
+              int a, b, d;
+              oz_pair(q, a, b, d);
+              const bool first_of_d = (q == 0 || q == 1 || q == 3 || q == 6);
+              const uint32_t a_addr = st + a * kOzHalfA + kk * 256;
+              const uint32_t b_addr = st + kOzS * kOzHalfA + b * kOzHalfB + kk * 256;
+              mma_bf16(tmem + buf * 256 + d * kOzBn, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc,
+                       (first && kk == 0 && first_of_d) ? 0u : 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+          if ((h % hc) == hc - 1 || h == kh - 1) {
+            mma_commit(&acc_full[buf]);
+            ++cg;
           }
         }
-        mma_commit(&empty[s]);
-        if ((kt % kOzChunkKt) == kOzChunkKt - 1 || kt == p.kt - 1) mma_commit(&acc_full[buf]);
       }
       if (!ok) {
         mma_commit(&acc_full[0]);
@@ -1621,35 +1646,39 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
   } else {
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    const int i = mt * kTileRows + row;  // output row of S_d X'
-    float hs[kOzBn], ls[kOzBn];
-#pragma unroll
-    for (int e = 0; e < kOzBn; ++e) { hs[e] = 0.f; ls[e] = 0.f; }
     bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const int buf = ch & 1;
-      if (!mbar_wait(&acc_full[buf], (ch >> 1) & 1, abort_flag)) { ok = false; break; }
-      tc_fence_after();
+    int cg = 0;
+    for (int u = blockIdx.x; u < units && ok; u += G) {
+      const int bidx = refined[u / per], rem = u % per;
+      const int mt = rem % m_tiles, nt = rem / m_tiles;
+      const int i = mt * kTileRows + row;  // output row of S_d X'
+      float hs[kOzBn], ls[kOzBn];
 #pragma unroll
-      for (int d = 0; d < kOzS; ++d) {
-        const float sc = ldexpf(1.0f, -kOzBits * (d + 2));
+      for (int e = 0; e < kOzBn; ++e) { hs[e] = 0.f; ls[e] = 0.f; }
+      for (int ch = 0; ch < nchunks; ++ch, ++cg) {
+        const int buf = cg & 1;
+        if (!mbar_wait(&acc_full[buf], (cg >> 1) & 1, abort_flag)) { ok = false; break; }
+        tc_fence_after();
 #pragma unroll
-        for (int pc = 0; pc < kOzBn / 32; ++pc) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + d * kOzBn + pc * 32, v);
+        for (int d = 0; d < kOzS; ++d) {
+          const float sc = ldexpf(1.0f, -kOzBits * (d + 2));
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            float s, er;
-            two_sum(hs[pc * 32 + e], v[e] * sc, s, er);
-            hs[pc * 32 + e] = s;
-            ls[pc * 32 + e] += er;
+          for (int pc = 0; pc < kOzBn / 32; ++pc) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + d * kOzBn + pc * 32, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              float s, er;
+              two_sum(hs[pc * 32 + e], v[e] * sc, s, er);
+              hs[pc * 32 + e] = s;
+              ls[pc * 32 + e] += er;
+            }
           }
         }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
       }
-      tc_fence_before();
-      mbar_arrive(&acc_empty[buf]);
-    }
-    if (ok && !*abort_flag) {
+      if (!ok || *abort_flag) break;
       const int n = p.c.n, np = p.np;
       const bool sh = shifted_point(p.m, p.eps[p.q0 + bidx]);
       const int r = (i < n && sh) ? (i == 0 ? n - 1 : i - 1) : i;  // row of R' fed by row i
@@ -1662,18 +1691,18 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
       const int kt = 2 * np / kTileK;
       const int j0 = nt * (kOzBn / 2);
 #pragma unroll
-      for (int u = 0; u < kOzBn / 2; ++u) {
-        const int j = j0 + u;
+      for (int uu = 0; uu < kOzBn / 2; ++uu) {
+        const int j = j0 + uu;
         const int sc = ei + xe[j];
-        float tr_h = ldexpf(hs[2 * u], sc), tr_l = ldexpf(ls[2 * u], sc);
-        float ti_h = ldexpf(hs[2 * u + 1], sc), ti_l = ldexpf(ls[2 * u + 1], sc);
+        float tr_h = ldexpf(hs[2 * uu], sc), tr_l = ldexpf(ls[2 * uu], sc);
+        float ti_h = ldexpf(hs[2 * uu + 1], sc), ti_l = ldexpf(ls[2 * uu + 1], sc);
         // T - (B - S_sp) X' at (i, j), double-float
         auto sub_prod = [&](float4 co, float2 xv) {
-          float h, l;
-          df_mul_f(co.x, co.y, xv.x, h, l); df_add(tr_h, tr_l, -h, -l);  // - c_re x_re
-          df_mul_f(co.z, co.w, xv.y, h, l); df_add(tr_h, tr_l, h, l);    // + c_im x_im
-          df_mul_f(co.x, co.y, xv.y, h, l); df_add(ti_h, ti_l, -h, -l);  // - c_re x_im
-          df_mul_f(co.z, co.w, xv.x, h, l); df_add(ti_h, ti_l, -h, -l);  // - c_im x_re
+          float hh, ll;
+          df_mul_f(co.x, co.y, xv.x, hh, ll); df_add(tr_h, tr_l, -hh, -ll);  // - c_re x_re
+          df_mul_f(co.z, co.w, xv.y, hh, ll); df_add(tr_h, tr_l, hh, ll);    // + c_im x_im
+          df_mul_f(co.x, co.y, xv.y, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_re x_im
+          df_mul_f(co.z, co.w, xv.x, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_im x_re
         };
         sub_prod(cd, x[(size_t)i * np + j]);
         if (i >= 1 && i < n) sub_prod(cs, x[(size_t)(i - 1) * np + j]);
@@ -1695,8 +1724,10 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(OzParams p) {
   }
   __syncthreads();
   if (warp == 1) {
-    for (int s = 0; s < 2 && s < nchunks; ++s) {
-      const int last = ((nchunks - 1 - s) / 2) * 2 + s;  // last chunk that used buffer s
+    // every MMA of this CTA has completed before the TMEM is released
+    const int chunks = ((units - (int)blockIdx.x + G - 1) / G > 0 ? (units - (int)blockIdx.x + G - 1) / G : 0) * nchunks;
+    for (int s = 0; s < 2 && s < chunks; ++s) {
+      const int last = ((chunks - 1 - s) / 2) * 2 + s;  // last chunk that used buffer s
       const uint64_t t0 = global_ns();
       while (!mbar_test(&acc_full[s], (last >> 1) & 1) && global_ns() - t0 < kWaitNs) {
       }
@@ -1724,7 +1755,6 @@ struct EpiStore {
 // gloc (= or +=) sum_b wq (X' + flag dX')[i][col(j)], b ascending.  The sum
 // runs in double-float (hi + lo FP32 pairs); w_q is split into hi + lo and
 // X' is exact in FP32, so w_q X' is formed exactly (two-product).
-constexpr int kRedMaxBatch = 512;
 __global__ void __launch_bounds__(256) reduce_refined_kernel(ContourDev c, ModelDev m,
                                                              const double* __restrict__ eps_d,
                                                              const double* __restrict__ wq_d, int q0, int nb,
@@ -1848,6 +1878,24 @@ int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const dou
   return NEDMFT_OK;
 }
 
+namespace {
+// 4-D tensor map over `tiles` packed 128 x 64 bf16 tiles at `base`, moved in
+// half tiles of `rgroups` 8-row groups: box (64 elements, 4 core columns, rgroups, 1).
+int encode_oz_map(CUtensorMap* map, void* base, uint64_t tiles, uint32_t rgroups) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[4] = {64, 8, 16, tiles};
+  const cuuint64_t strides[3] = {128, 1024, 16384};
+  const cuuint32_t box[4] = {64, 4, rgroups, 1};
+  const cuuint32_t elem_strides[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, elem_strides,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled (residual) failed (CUresult %d)", (int)r);
+  return NEDMFT_OK;
+}
+}  // namespace
+
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
                        const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
                        char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
@@ -1878,17 +1926,30 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
   NED_LAUNCH_CHECK("oz_pack_x_kernel");
   {
     OzParams p{};
-    p.a = sh.sd_img; p.a_slice = sh.sd_slice; p.a_exp = sh.sd_exp;
-    p.b = ximg; p.b_batch = kOzS * xs; p.b_slice = xs; p.b_exp = xexp;
+    const uint64_t xs_tiles = (uint64_t)xs / kTileElems;  // tiles per X' slice
+    if ((rc = encode_oz_map(&p.a_map, sh.sd_img, (uint64_t)kOzS * sh.sd_slice / kTileElems, 16))) return rc;
+    if ((rc = encode_oz_map(&p.b_map, ximg, (uint64_t)nb * kOzS * xs_tiles, 8))) return rc;
+    p.a_slice = (long long)(sh.sd_slice / kTileElems);
+    p.b_batch = (long long)(kOzS * xs_tiles);
+    p.b_slice = (long long)xs_tiles;
+    p.a_exp = sh.sd_exp;
+    p.b_exp = xexp;
     p.X = X; p.coef = coef; p.flags = sh.flags;
     p.rimg = rimg; p.r_batch = 2 * rs; p.r_slice = rs;
-    p.c = c; p.m = m; p.eps = eps; p.q0 = q0; p.np = np; p.kt = 2 * np / kTileK; p.status = status;
+    p.c = c; p.m = m; p.eps = eps; p.q0 = q0; p.nb = nb; p.np = np; p.kt = 2 * np / kTileK; p.status = status;
+    if (nb > kRedMaxBatch) return set_error(NEDMFT_EINVAL, "residual: batch %d > %d", nb, kRedMaxBatch);
     static bool attr = false;
     if (!attr) {
       NED_CUDA(cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
       attr = true;
     }
-    oz_residual_kernel<<<dim3(np / kTileRows, 2 * np / kOzBn, nb), 192, kOzSmem, st>>>(p);
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      NED_CUDA(cudaGetDevice(&dev));
+      NED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    oz_residual_kernel<<<sms, 192, kOzSmem, st>>>(p);
     NED_LAUNCH_CHECK("oz_residual_kernel");
   }
   {  // dX' = X' R' (bf16x3), refined points only
