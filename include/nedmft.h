@@ -146,6 +146,38 @@ int nedmft_quadrature_grid(int32_t n, double* eps_host, double* ebar_host,
 int nedmft_quadrature_grid_avg(int32_t n, double* eps_host, double* ebar_host,
                                double* wq_host);
 
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Equal-time moments of the retarded Green's function (Sec. II, the
+ * paragraph on moments after Eq. current_def), on the upper-branch times t_m,
+ * m = 0 .. N_t - 1.  With G^R(t, t') = G^>(t, t') - G^<(t, t') read from the
+ * contour matrix (G^> = element (lower-branch row of t, upper row of t'),
+ * G^< = (upper row of t, lower row of t'); the lower-branch row of t_m is
+ * 2 N_t - m) and f(s) = i G^R(t_m + s/2, t_m - s/2) = mu0 - i mu1 s - mu2 s^2/2
+ * + O(s^3), the quadratic through s = 2 dt, 4 dt, 6 dt gives mu0, mu1, mu2
+ * (exact values at half filling: 1, 0, 1/2 + U^2/4; the discrete ones carry
+ * O(dt) errors that the dt -> 0 extrapolation removes).
+ *   gloc_d: N_c x N_c complex128 on the device (any contour Green's function).
+ *   mu0_d, mu1_d, mu2_d: N_t doubles each, NaN where t_m +- 3 dt leaves the
+ *   real-time window; dens_d: N_t doubles, n(t_m) = -i G^<(t_m, t_m).  Any
+ *   output may be NULL.  Stream-ordered; EINVAL for a NULL gloc or a bad contour. */
+int nedmft_moments(const nedmft_contour* c, const nedmft_c128* gloc_d,
+                   double* mu0_d, double* mu1_d, double* mu2_d, double* dens_d,
+                   void* stream);
+
+/* Nonequilibrium density of states (Eqs. gr_omega, dos_def):
+ * rho(T, omega) = -Im G^R(T, omega) / pi with G^R(T, omega) the integral over
+ * t_rel >= 0 of exp(i omega t_rel) G^R(T + t_rel/2, T - t_rel/2), evaluated by
+ * the trapezoid rule over the symmetric pairs (t_{m+k}, t_{m-k}),
+ * k = 0 .. min(m, N_t - 1 - m), step 2 dt, with no window.
+ *   m_d: n_avg average-time indices T = t_m on the device (an index outside
+ *   [0, N_t) yields NaN); omega_d: n_omega frequencies on the device;
+ *   rho_d: n_avg x n_omega doubles, row-major.  With n_avg or n_omega zero
+ *   nothing is written and the arrays may be NULL.  Stream-ordered. */
+int nedmft_dos(const nedmft_contour* c, const nedmft_c128* gloc_d,
+               const int32_t* m_d, int32_t n_avg, const double* omega_d,
+               int32_t n_omega, double* rho_d, void* stream);
+
 /* ---------------------------------------------------------------- G0 */
 
 /* Noninteracting contour Green's function of Eq. g_contour_non_final2 for

@@ -20,7 +20,8 @@ correlated material", Sec. II):
 * the current (Eq. current_def), the Falicov-Kimball impurity update
   (Eqs. effective_medium, dynamical_mean_field, g_imp_solve, the M matrix of
   the discretised ``(i d/dt + mu) delta_c``, Eq. matrix_inverse_discrete), the
-  plain-substitution DMFT loop, and Lagrange extrapolation to dt -> 0.
+  plain-substitution DMFT loop, Lagrange extrapolation to dt -> 0, and the
+  accuracy diagnostics (equal-time moments, Eqs. gr_omega and dos_def).
 
 Everything is complex128 / float64.  Library primitives used as single steps:
 ``numpy.linalg.solve``, ``numpy.linalg.inv``, ``numpy.linalg.eigh``.
@@ -49,6 +50,16 @@ R8  ``G^<(t_m, t_m)`` is the element (upper index m, lower index of the same
 R9  E = 0 uses the limit ``F(s) = eps s`` of the band phase.
 R10 Convergence: ``max|G_new - G_old| / max|G_new| < tol``, plain substitution
     ``Sigma <- Sigma_new``, Sigma starting at 0.
+R11 Equal-time moments (the moments paragraph after Eq. current_def): with
+    ``G^R(t, t') = G^>(t, t') - G^<(t, t')`` on the real branches and
+    ``f(s) = i G^R(T + s/2, T - s/2) = mu0 - i mu1 s - mu2 s^2 / 2 + O(s^3)``, the
+    moments at T = t_m come from the quadratic through the relative times
+    s = 2 k dt, k = 1, 2, 3 (pairs t_{m+k}, t_{m-k}); the paper's "first two
+    derivatives at equal time".  Exact values at half filling: mu0 = 1,
+    mu1 = 0, mu2 = 1/2 + U^2/4 (t* = 1).
+R12 Density of states (Eqs. gr_omega, dos_def): the relative-time integral is
+    the trapezoid rule over the symmetric pairs t_{m+k}, t_{m-k},
+    k = 0 .. min(m, N_t - 1 - m), step 2 dt, no window.
 """
 
 from __future__ import annotations
@@ -354,6 +365,62 @@ def dmft_solve(c: Contour, model: Model, n_quad: int, tol: float = 1e-8,
         g_old = gloc
         sigma, _ = impurity_update(c, model, gloc, sigma)
     return DmftResult(sigma, gloc, jc, max_iter, err, False)
+
+
+# --------------------------------------------------------------------------
+# Diagnostics: equal-time moments and the nonequilibrium density of states
+# (Sec. II, the moments paragraph; Eqs. gr_omega, dos_def)
+# --------------------------------------------------------------------------
+
+
+def real_time_rows(c: Contour, m: int) -> tuple[int, int]:
+    """Contour rows of real time t_m: upper-branch row m and its lower-branch
+    partner (reading R8: for t_min the partner is the first imaginary point)."""
+    return m, 2 * c.n_t - m
+
+
+def retarded(c: Contour, g: np.ndarray, i: int, j: int) -> complex:
+    """G^R(t_i, t_j) = G^>(t_i, t_j) - G^<(t_i, t_j) for i >= j.
+
+    On the contour, G^> is the element (later branch row, earlier branch
+    column) = (lower row of t_i, upper row of t_j); G^< = (upper of t_i, lower of t_j).
+    """
+    ui, li = real_time_rows(c, i)
+    uj, lj = real_time_rows(c, j)
+    return g[li, uj] - g[ui, lj]
+
+
+def moments(c: Contour, g: np.ndarray):
+    """(mu0, mu1, mu2, n) on the upper-branch times (reading R11); NaN where
+    the three pairs leave the real-time window.  n(t) = -i G^<(t, t)."""
+    nt = c.n_t
+    mu0 = np.full(nt, np.nan)
+    mu1 = np.full(nt, np.nan)
+    mu2 = np.full(nt, np.nan)
+    s = 2.0 * c.dt * np.arange(1, 4)
+    for m in range(3, nt - 3):
+        f = np.array([1j * retarded(c, g, m + k, m - k) for k in range(1, 4)])
+        c2, c1, c0 = np.polyfit(s, f, 2)  # f(s) = c0 + c1 s + c2 s^2
+        mu0[m] = c0.real
+        mu1[m] = (1j * c1).real
+        mu2[m] = (-2.0 * c2).real
+    return mu0, mu1, mu2, density(c, g).real
+
+
+def dos(c: Contour, g: np.ndarray, m: int, omega) -> np.ndarray:
+    """rho(T = t_m, omega) = -Im G^R(T, omega) / pi (Eqs. gr_omega, dos_def),
+    G^R(T, omega) = integral over t_rel >= 0 of exp(i omega t_rel) G^R(T + t_rel/2, T - t_rel/2)
+    by the trapezoid rule (reading R12)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    kmax = min(m, c.n_t - 1 - m)
+    h = 2.0 * c.dt
+    out = np.zeros(omega.shape, dtype=np.complex128)
+    if kmax == 0:  # no relative-time interval at the edges of the window
+        return out.real
+    for k in range(kmax + 1):
+        wk = 0.5 if k in (0, kmax) else 1.0
+        out += wk * h * np.exp(1j * omega * (k * h)) * retarded(c, g, m + k, m - k)
+    return -out.imag / np.pi
 
 
 # --------------------------------------------------------------------------

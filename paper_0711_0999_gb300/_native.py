@@ -67,6 +67,8 @@ SIGNATURES = {
     "nedmft_quadrature_grid_avg": (ctypes.c_int, [c_int32, PD, PD, PD]),
     "nedmft_extrapolate_current": (ctypes.c_int, [c_int32, PD, PD, PI, ctypes.POINTER(c_void_p), c_void_p, c_int32,
                                                   c_void_p, c_void_p, c_void_p]),
+    "nedmft_moments": (ctypes.c_int, [PC, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nedmft_dos": (ctypes.c_int, [PC, c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p]),
     "nedmft_g0_build": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "nedmft_lattice_workspace_size": (c_size_t, [PC, c_int32, ctypes.c_int, c_int32]),
     "nedmft_lattice_gloc": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_int,

@@ -173,6 +173,26 @@ def current(grid: Grid, model: N.Model, sigma, eps, ebar, wq, precision="fp64", 
     return j, ji
 
 
+def moments(grid: Grid, gloc: torch.Tensor, stream=None):
+    """(mu0, mu1, mu2, n) on the upper-branch times: the equal-time moments of G^R and the density."""
+    dev = gloc.device
+    out = [torch.empty(grid.n_t, dtype=torch.float64, device=dev) for _ in range(4)]
+    N.check(N.lib().nedmft_moments(ctypes.byref(grid.contour), _ptr(gloc), *[_ptr(o) for o in out],
+                                   ctypes.c_void_p(_stream(stream))))
+    return tuple(out)
+
+
+def dos(grid: Grid, gloc: torch.Tensor, m_index, omega, stream=None) -> torch.Tensor:
+    """rho(t_m, omega), one row per average-time index m."""
+    dev = gloc.device
+    m_t = torch.as_tensor(np.asarray(m_index, dtype=np.int32), device=dev)
+    om = _dev(omega, torch.float64, dev)
+    rho = torch.empty((m_t.numel(), om.numel()), dtype=torch.float64, device=dev)
+    N.check(N.lib().nedmft_dos(ctypes.byref(grid.contour), _ptr(gloc), _ptr(m_t), m_t.numel(), _ptr(om), om.numel(),
+                               _ptr(rho), ctypes.c_void_p(_stream(stream))))
+    return rho
+
+
 def impurity_update(grid: Grid, model: N.Model, gloc: torch.Tensor, sigma: torch.Tensor, want_gimp=False,
                     ws=None, stream=None):
     dev = gloc.device

@@ -70,6 +70,40 @@ DmftLayout dmft_layout(const nedmft_contour& c, int n_quad, nedmft_precision pre
   return L;
 }
 
+// A private non-blocking stream that starts after `user` and that `user`
+// waits for when the scope closes.
+struct StreamScope {
+  cudaStream_t user = nullptr, ws = nullptr;
+  cudaEvent_t ev = nullptr;
+  int open(cudaStream_t u) {
+    user = u;
+    NED_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+    NED_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    NED_CUDA(cudaEventRecord(ev, user));
+    NED_CUDA(cudaStreamWaitEvent(ws, ev, 0));
+    return NEDMFT_OK;
+  }
+  ~StreamScope() {
+    if (ws) {
+      if (ev) {
+        cudaEventRecord(ev, ws);
+        cudaStreamWaitEvent(user, ev, 0);
+      }
+      cudaStreamDestroy(ws);
+    }
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+struct GraphScope {
+  cudaGraph_t* g;
+  cudaGraphExec_t* e;
+  ~GraphScope() {
+    for (int i = 0; i < 2; ++i) {
+      if (e[i]) cudaGraphExecDestroy(e[i]);
+      if (g[i]) cudaGraphDestroy(g[i]);
+    }
+  }
+};
 }  // namespace
 }  // namespace nedmft
 
@@ -93,7 +127,16 @@ extern "C" int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
   if (need == 0) return set_error(NEDMFT_EINVAL, "dmft_solve: invalid contour or precision");
   if (ws_bytes < need) return set_error(NEDMFT_ENOMEM, "dmft_solve: workspace %zu < %zu", ws_bytes, need);
   if (((uintptr_t)ws_d) & 255) return set_error(NEDMFT_EINVAL, "dmft_solve: workspace not 256-byte aligned");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the loop runs on a private stream ordered after the caller's (graph
+  // capture is not possible on the legacy default stream); the caller's stream
+  // waits for it when the scope closes
+  StreamScope scope;
+  int src = scope.open(static_cast<cudaStream_t>(stream));
+  if (src) return src;
+  cudaStream_t st = scope.ws;
+  cudaGraph_t graph_of[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec_of[2] = {nullptr, nullptr};
+  GraphScope gscope{graph_of, exec_of};
   DmftLayout L = dmft_layout(*c, n_quad, prec);
   const int nq = n_quad * n_quad;
   const size_t n = c->n_c, nn = n * n;
@@ -124,37 +167,52 @@ extern "C" int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
   else
     NED_CUDA(cudaMemsetAsync(s[0], 0, sizeof(double2) * nn, st));
 
-  int cur = 0, gcur = 0;
   double e_host = INFINITY;
-  int it = 0;
+  int it = 1;
   bool conv = false;
-  for (it = 1; it <= max_iter; ++it) {
-    rc = lattice_run(*c, *m, s[cur], eps, ebar, wq, nq, prec, g[gcur], j_d, nullptr, lat_ws, L.lat, st);
-    if (rc) return rc;
-    if (it > 1) {
-      norm_pass1<<<kNormBlocks, 256, 0, st>>>(g[gcur], g[1 - gcur], nn, part);
-      NED_LAUNCH_CHECK("norm_pass1");
-      norm_pass2<<<1, 32, 0, st>>>(part, kNormBlocks, err_d);
-      NED_LAUNCH_CHECK("norm_pass2");
-      NED_CUDA(cudaMemcpyAsync(&e_host, err_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-      NED_CUDA(cudaStreamSynchronize(st));
-      int ds = nedmft_check_status(stream);
-      if (ds) return ds;
-      if (e_host < tol) { conv = true; break; }
+  // Iteration 1 runs eagerly on the private stream; every later iteration --
+  // impurity step, lattice step, convergence norm -- is one CUDA-graph launch.
+  // graph[par] takes (g[par], s[par]) to s[1 - par], g[1 - par] and the norm of
+  // g[1 - par] - g[par]; the iterations alternate par = 0, 1, 0, ...
+  rc = lattice_run(*c, *m, s[0], eps, ebar, wq, nq, prec, g[0], j_d, nullptr, lat_ws, L.lat, st);
+  if (rc) return rc;
+  int cur = 0;  // s[cur], g[cur] hold the latest pair
+  if (max_iter > 1) {
+    for (int par = 0; par < 2; ++par) {
+      NED_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int crc = nedmft_impurity_update(c, m, reinterpret_cast<const nedmft_c128*>(g[par]),
+                                       reinterpret_cast<const nedmft_c128*>(s[par]),
+                                       reinterpret_cast<nedmft_c128*>(s[1 - par]), nullptr, imp_ws, L.imp, st);
+      if (!crc)
+        crc = lattice_run(*c, *m, s[1 - par], eps, ebar, wq, nq, prec, g[1 - par], j_d, nullptr, lat_ws, L.lat, st);
+      if (!crc) {
+        norm_pass1<<<kNormBlocks, 256, 0, st>>>(g[1 - par], g[par], nn, part);
+        norm_pass2<<<1, 32, 0, st>>>(part, kNormBlocks, err_d);
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      graph_of[par] = graph;
+      if (crc) return crc;
+      if (ce != cudaSuccess) return cuda_fail(ce, "dmft_solve: capture of the iteration");
+      NED_CUDA(cudaGraphInstantiate(&exec_of[par], graph, 0));
     }
-    if (it == max_iter) break;
-    rc = nedmft_impurity_update(c, m, reinterpret_cast<const nedmft_c128*>(g[gcur]),
-                                reinterpret_cast<const nedmft_c128*>(s[cur]), reinterpret_cast<nedmft_c128*>(s[1 - cur]),
-                                nullptr, imp_ws, L.imp, stream);
-    if (rc) return rc;
-    cur = 1 - cur;
-    gcur = 1 - gcur;
   }
+  for (it = 2; it <= max_iter; ++it) {
+    const int par = cur;
+    NED_CUDA(cudaGraphLaunch(exec_of[par], st));
+    NED_CUDA(cudaMemcpyAsync(&e_host, err_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NED_CUDA(cudaStreamSynchronize(st));
+    cur = 1 - par;
+    int ds = nedmft_check_status(st);
+    if (ds) return ds;
+    if (e_host < tol) { conv = true; break; }
+  }
+  const int gcur = cur;
   if (it > max_iter) it = max_iter;
   NED_CUDA(cudaMemcpyAsync(gloc_d, g[gcur], sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
   NED_CUDA(cudaMemcpyAsync(sigma_d, s[cur], sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st));
   NED_CUDA(cudaStreamSynchronize(st));
-  int ds = nedmft_check_status(stream);
+  int ds = nedmft_check_status(st);
   if (ds) return ds;
   if (iters) *iters = it;
   if (err) *err = e_host;
