@@ -229,6 +229,31 @@ int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
                    nedmft_precision prec, double* j_d, double* j_imag_d,
                    void* ws_d, size_t ws_bytes, void* stream);
 
+/* Batch autotuner (scope table: the tile/batch choice per N_c).  Times one
+ * lattice step (after an untimed one) with each candidate number of points
+ * per batch that fits the workspace, and records the fastest for this
+ * (n_c, nq, prec); later calls of nedmft_lattice_workspace_size(..., batch = 0),
+ * nedmft_lattice_gloc, nedmft_current and the DMFT drivers in this process use
+ * it.  Tune before sizing workspaces: a workspace sized for the former batch
+ * may be too small afterwards (ENOMEM, never an overrun).
+ *   Arguments 1-8 as nedmft_lattice_gloc (Sigma and the points are the ones
+ *   to time with); candidates: n_candidates batch sizes on the host;
+ *   best_batch, best_ms: host outputs (may be NULL).  Synchronises the stream.
+ *   ENOMEM if no candidate fits ws_bytes. */
+int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_model* m,
+                            const nedmft_c128* sigma_d, const double* eps_d,
+                            const double* ebar_d, const double* wq_d,
+                            int32_t nq, nedmft_precision prec,
+                            const int32_t* candidates, int32_t n_candidates,
+                            int32_t* best_batch, double* best_ms,
+                            void* ws_d, size_t ws_bytes, void* stream);
+
+/* Points per batch that nedmft_lattice_gloc uses for (c, nq, prec): the tuned
+ * size if nedmft_lattice_autotune ran for them, else the default (clamped to
+ * nq).  0 for invalid arguments. */
+int32_t nedmft_lattice_batch(const nedmft_contour* c, int32_t nq,
+                             nedmft_precision prec);
+
 /* The lattice step for small contours (n_c <= 112), FP64 arithmetic, with
  * no workspace argument and no device allocation of any kind.  The paper has
  * no counterpart to this entry point: it exists for callers that cannot
@@ -362,6 +387,34 @@ int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
                       int32_t max_iter, nedmft_c128* sigma_d,
                       nedmft_c128* gloc_d, double* j_d, int32_t* iters,
                       double* err, void* ws_d, size_t ws_bytes, void* stream);
+
+/* Several DMFT runs at once (scope table: ragged batching of many (U, E, dt)
+ * runs): run r has its own contour (n_c may differ between runs) and model,
+ * all share n_quad and prec.  Every sweep takes one iteration of each run that
+ * is still active -- impurity step, lattice step, convergence norm, all on one
+ * stream without a host sync in between -- and synchronises once; a run leaves
+ * the sweep when it converges (same norm as nedmft_dmft_solve) or reaches
+ * max_iter.  The points of different runs are not mixed within a Gauss-Jordan
+ * batch: each run's own points fill its batches.
+ *   contours, models: host arrays of n_runs; sigma_init_d: NULL (all runs
+ *   start at Sigma = 0) or a host array of n_runs device pointers, each NULL
+ *   or N_c(r)^2 complex128; sigma_d, gloc_d: host arrays of n_runs device
+ *   pointers (N_c(r)^2 complex128 outputs, as nedmft_dmft_solve); j_d: NULL
+ *   or a host array of n_runs device pointers (N_t(r) doubles, each may be
+ *   NULL); iters, errs, converged: host arrays of n_runs (may be NULL).
+ *   Workspace: nedmft_dmft_batch_workspace_size bytes, 256-byte aligned.
+ *   Returns ENOTCONV (> 0) if any run did not converge. */
+size_t nedmft_dmft_batch_workspace_size(int32_t n_runs,
+                                        const nedmft_contour* contours,
+                                        int32_t n_quad, nedmft_precision prec);
+int nedmft_dmft_solve_batch(int32_t n_runs, const nedmft_contour* contours,
+                            const nedmft_model* models, int32_t n_quad,
+                            nedmft_precision prec,
+                            const nedmft_c128* const* sigma_init_d, double tol,
+                            int32_t max_iter, nedmft_c128* const* sigma_d,
+                            nedmft_c128* const* gloc_d, double* const* j_d,
+                            int32_t* iters, double* errs, int32_t* converged,
+                            void* ws_d, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

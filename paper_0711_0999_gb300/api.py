@@ -173,6 +173,35 @@ def current(grid: Grid, model: N.Model, sigma, eps, ebar, wq, precision="fp64", 
     return j, ji
 
 
+def lattice_autotune(grid: Grid, model: N.Model, sigma, eps, ebar, wq, precision="mixed_bf16", candidates=None,
+                     stream=None):
+    """Times one lattice step per candidate batch size and makes the fastest the
+    default for (n_c, nq, precision) in this process; returns (batch, ms)."""
+    dev = sigma.device if isinstance(sigma, torch.Tensor) else torch.device("cuda")
+    sigma_t = _dev(sigma, torch.complex128, dev)
+    eps_t, ebar_t, wq_t = (_dev(a, torch.float64, dev) for a in (eps, ebar, wq))
+    nq = eps_t.numel()
+    p = _prec(precision)
+    if candidates is None:
+        candidates = [76, 114, 152, 228, 304]
+    cand = (N.c_int32 * len(candidates))(*candidates)
+    need = max(N.lib().nedmft_lattice_workspace_size(ctypes.byref(grid.contour), nq, p, int(b)) for b in candidates)
+    if need == 0:
+        raise NedmftError(N.NEDMFT_EINVAL, "lattice_workspace_size: invalid arguments")
+    ws = workspace(need, dev)
+    best = N.c_int32(0)
+    ms = N.c_double(0.0)
+    N.check(N.lib().nedmft_lattice_autotune(ctypes.byref(grid.contour), ctypes.byref(model), _ptr(sigma_t),
+                                            _ptr(eps_t), _ptr(ebar_t), _ptr(wq_t), nq, p, cand, len(candidates),
+                                            ctypes.byref(best), ctypes.byref(ms), _ptr(ws), ws.numel(),
+                                            ctypes.c_void_p(_stream(stream))))
+    return best.value, ms.value
+
+
+def lattice_batch(grid: Grid, nq: int, precision="mixed_bf16") -> int:
+    return int(N.lib().nedmft_lattice_batch(ctypes.byref(grid.contour), nq, _prec(precision)))
+
+
 def moments(grid: Grid, gloc: torch.Tensor, stream=None):
     """(mu0, mu1, mu2, n) on the upper-branch times: the equal-time moments of G^R and the density."""
     dev = gloc.device
@@ -235,3 +264,29 @@ def dmft_solve(grid: Grid, model: N.Model, n_quad: int, precision="fp64", sigma_
                                    ctypes.byref(err), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(stream)))
     N.check(rc, allow_warning=True)
     return DmftSolution(sigma, gloc, j, it.value, err.value, rc == N.NEDMFT_OK)
+
+
+def dmft_solve_batch(grids, models, n_quad: int, precision="fp64", sigma_init=None, tol=1e-8, max_iter=50,
+                     device="cuda", stream=None):
+    """Several DMFT runs swept together (nedmft_dmft_solve_batch); one DmftSolution per run."""
+    n = len(grids)
+    assert len(models) == n and n >= 1
+    p = _prec(precision)
+    cs = (N.Contour * n)(*[g.contour for g in grids])
+    ms = (N.Model * n)(*models)
+    need = N.lib().nedmft_dmft_batch_workspace_size(n, cs, n_quad, p)
+    if need == 0:
+        raise NedmftError(N.NEDMFT_EINVAL, "dmft_batch_workspace_size: invalid arguments")
+    ws = workspace(need, device)
+    sig = [torch.empty((g.n_c, g.n_c), dtype=torch.complex128, device=device) for g in grids]
+    gl = [torch.empty((g.n_c, g.n_c), dtype=torch.complex128, device=device) for g in grids]
+    js = [torch.empty(g.n_t, dtype=torch.float64, device=device) for g in grids]
+    ptrs = lambda ts: (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in ts])
+    init = None if sigma_init is None else ptrs(sigma_init)
+    it = (N.c_int32 * n)()
+    err = (N.c_double * n)()
+    conv = (N.c_int32 * n)()
+    rc = N.lib().nedmft_dmft_solve_batch(n, cs, ms, n_quad, p, init, tol, max_iter, ptrs(sig), ptrs(gl), ptrs(js), it,
+                                         err, conv, _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(stream)))
+    N.check(rc, allow_warning=True)
+    return [DmftSolution(sig[r], gl[r], js[r], it[r], err[r], bool(conv[r])) for r in range(n)]

@@ -1,6 +1,9 @@
 // C-ABI entry points of the lattice step, the G0 builder and the DMFT loop.
 #include <math.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "lattice.cuh"
@@ -31,6 +34,16 @@ Path choose_path(const nedmft_contour& c, nedmft_precision p) {
 
 int padded_for(Path path, int n) { return path == Path::MixedUmma ? umma_padded(n) : padded(n); }
 
+// Batch sizes chosen by nedmft_lattice_autotune, per (n_c, nq, precision).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+int tuned_batch(const nedmft_contour& c, int nq, nedmft_precision prec) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(c.n_c, nq, (int)prec));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
 int default_batch(const nedmft_contour& c, int nq, Path path) {
   const size_t np = padded_for(path, c.n_c);
   size_t per = 0, budget = (size_t)40 << 30;  // about 40 GB of batch buffers
@@ -58,6 +71,7 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
   LatticeLayout L{};
   L.path = choose_path(c, prec);
   L.np = padded_for(L.path, c.n_c);
+  if (batch <= 0) batch = tuned_batch(c, nq, prec);
   L.mb = batch > 0 ? (batch < nq ? batch : nq) : default_batch(c, nq, L.path);
   const size_t n = c.n_c, np = L.np, mb = L.mb;
   L.S = align256(sizeof(double2) * n * n);
@@ -92,10 +106,21 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
 }  // namespace
 
 // The lattice step proper (also used by the current and the DMFT loop).
+int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
+                      const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
+                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts);
+
 int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
                 const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
                 double* ji, void* ws, size_t ws_bytes, cudaStream_t st) {
-  LatticeLayout L = lattice_layout(c, nq, prec, 0);
+  return lattice_run_batch(c, m, sigma, eps, ebar, wq, nq, prec, gloc, j, ji, ws, ws_bytes, st, 0);
+}
+
+// batch_pts > 0: points per batch (clamped to nq); 0: the tuned or default size
+int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
+                      const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
+                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts) {
+  LatticeLayout L = lattice_layout(c, nq, prec, batch_pts);
   if (ws_bytes < L.total) return set_error(NEDMFT_ENOMEM, "lattice: workspace %zu < %zu bytes", ws_bytes, L.total);
   int* status = device_status_ptr();
   if (!status) return set_error(NEDMFT_ECUDA, "lattice: no device status word");
@@ -228,4 +253,58 @@ extern "C" int nedmft_current(const nedmft_contour* c, const nedmft_model* m, co
   if (!j_d && !j_imag_d) return set_error(NEDMFT_EINVAL, "current: both outputs NULL");
   return lattice_run(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec, nullptr, j_d,
                      j_imag_d, ws_d, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_model* m, const nedmft_c128* sigma_d,
+                                       const double* eps_d, const double* ebar_d, const double* wq_d, int32_t nq,
+                                       nedmft_precision prec, const int32_t* candidates, int32_t n_candidates,
+                                       int32_t* best_batch, double* best_ms, void* ws_d, size_t ws_bytes,
+                                       void* stream) {
+  int rc = lattice_checks(c, m, sigma_d, eps_d, ebar_d, wq_d, nq, prec, ws_d);
+  if (rc) return rc;
+  if (!candidates || n_candidates < 1) return set_error(NEDMFT_EINVAL, "autotune: no candidates");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  NED_CUDA(cudaEventCreate(&e0));
+  NED_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_t = 0.f;
+  for (int k = 0; k < n_candidates && !rc; ++k) {
+    const int b = candidates[k];
+    if (b < 1) continue;
+    if (lattice_layout(*c, nq, prec, b).total > ws_bytes) continue;  // does not fit the workspace
+    // one untimed pass (first-use setup), one timed pass
+    for (int pass = 0; pass < 2 && !rc; ++pass) {
+      if (pass == 1) {
+        const cudaError_t e = cudaEventRecord(e0, st);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
+      }
+      rc = lattice_run_batch(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec,
+                             nullptr, nullptr, nullptr, ws_d, ws_bytes, st, b);
+    }
+    if (rc) break;
+    cudaError_t e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+    if (!best || ms < best_t) { best = b < nq ? b : nq; best_t = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (!best) return set_error(NEDMFT_ENOMEM, "autotune: no candidate batch fits the workspace of %zu bytes", ws_bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple(c->n_c, (int)nq, (int)prec)] = best;
+  }
+  if (best_batch) *best_batch = best;
+  if (best_ms) *best_ms = best_t;
+  return nedmft_check_status(stream);
+}
+
+extern "C" int32_t nedmft_lattice_batch(const nedmft_contour* c, int32_t nq, nedmft_precision prec) {
+  if (!valid_contour(c) || nq < 1) return 0;
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32) return 0;
+  return lattice_layout(*c, nq, prec, 0).mb;
 }

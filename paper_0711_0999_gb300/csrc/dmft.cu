@@ -218,3 +218,166 @@ extern "C" int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
   if (err) *err = e_host;
   return conv ? NEDMFT_OK : NEDMFT_ENOTCONV;
 }
+
+// ------------------------------------------------------------------ several runs
+
+namespace {
+
+struct BatchLayout {
+  size_t quad, per_run_total, part, errs, lat, imp, total;
+  std::vector<size_t> run_off;  // offset of run r's (g[2], s[2]) block
+};
+
+BatchLayout batch_layout(int n_runs, const nedmft_contour* cs, int n_quad, nedmft_precision prec) {
+  BatchLayout L{};
+  const size_t nq = (size_t)n_quad * n_quad;
+  L.quad = 3 * align256(sizeof(double) * nq);
+  L.run_off.resize(n_runs);
+  size_t off = 0;
+  for (int r = 0; r < n_runs; ++r) {
+    L.run_off[r] = off;
+    const size_t nn = (size_t)cs[r].n_c * cs[r].n_c;
+    off += 4 * align256(sizeof(double2) * nn);
+    const size_t lat = nedmft_lattice_workspace_size(&cs[r], (int)nq, prec, 0);
+    const size_t imp = nedmft_impurity_workspace_size(&cs[r]);
+    if (lat > L.lat) L.lat = lat;
+    if (imp > L.imp) L.imp = imp;
+  }
+  L.per_run_total = off;
+  L.part = align256(sizeof(double) * 2 * kNormBlocks);
+  L.errs = align256(sizeof(double) * (size_t)n_runs);
+  L.lat = align256(L.lat);
+  L.imp = align256(L.imp);
+  L.total = L.quad + L.per_run_total + L.part + L.errs + L.lat + L.imp + 256;
+  return L;
+}
+
+}  // namespace
+
+extern "C" size_t nedmft_dmft_batch_workspace_size(int32_t n_runs, const nedmft_contour* contours, int32_t n_quad,
+                                                   nedmft_precision prec) {
+  if (n_runs < 1 || !contours || n_quad < 1 || n_quad > 512) return 0;
+  for (int r = 0; r < n_runs; ++r)
+    if (nedmft_lattice_workspace_size(&contours[r], n_quad * n_quad, prec, 0) == 0) return 0;
+  return batch_layout(n_runs, contours, n_quad, prec).total;
+}
+
+extern "C" int nedmft_dmft_solve_batch(int32_t n_runs, const nedmft_contour* contours, const nedmft_model* models,
+                                       int32_t n_quad, nedmft_precision prec,
+                                       const nedmft_c128* const* sigma_init_d, double tol, int32_t max_iter,
+                                       nedmft_c128* const* sigma_d, nedmft_c128* const* gloc_d, double* const* j_d,
+                                       int32_t* iters, double* errs, int32_t* converged, void* ws_d, size_t ws_bytes,
+                                       void* stream) {
+  if (n_runs < 1 || !contours || !models || !sigma_d || !gloc_d || !ws_d)
+    return set_error(NEDMFT_EINVAL, "dmft_solve_batch: NULL argument or no runs");
+  if (max_iter < 1 || !(tol > 0.0)) return set_error(NEDMFT_EINVAL, "dmft_solve_batch: max_iter < 1 or tol <= 0");
+  const size_t need = nedmft_dmft_batch_workspace_size(n_runs, contours, n_quad, prec);
+  if (need == 0) return set_error(NEDMFT_EINVAL, "dmft_solve_batch: invalid contour, n_quad or precision");
+  if (ws_bytes < need) return set_error(NEDMFT_ENOMEM, "dmft_solve_batch: workspace %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws_d) & 255) return set_error(NEDMFT_EINVAL, "dmft_solve_batch: workspace not 256-byte aligned");
+  for (int r = 0; r < n_runs; ++r)
+    if (!sigma_d[r] || !gloc_d[r]) return set_error(NEDMFT_EINVAL, "dmft_solve_batch: run %d has a NULL output", r);
+  StreamScope scope;
+  int rc = scope.open(static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  cudaStream_t st = scope.ws;
+  const BatchLayout L = batch_layout(n_runs, contours, n_quad, prec);
+  const int nq = n_quad * n_quad;
+  char* base = static_cast<char*>(ws_d);
+  double* eps = reinterpret_cast<double*>(base);
+  double* ebar = reinterpret_cast<double*>(base + align256(sizeof(double) * nq));
+  double* wq = reinterpret_cast<double*>(base + 2 * align256(sizeof(double) * nq));
+  char* runs = base + L.quad;
+  double* part = reinterpret_cast<double*>(runs + L.per_run_total);
+  double* err_d = reinterpret_cast<double*>(reinterpret_cast<char*>(part) + L.part);
+  void* lat_ws = reinterpret_cast<char*>(err_d) + L.errs;
+  void* imp_ws = static_cast<char*>(lat_ws) + L.lat;
+  std::vector<double> he(nq), hb(nq), hw(nq);
+  if ((rc = nedmft_quadrature_grid(n_quad, he.data(), hb.data(), hw.data()))) return rc;
+  NED_CUDA(cudaMemcpyAsync(eps, he.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaMemcpyAsync(ebar, hb.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaMemcpyAsync(wq, hw.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+
+  struct Run {
+    double2* g[2];
+    double2* s[2];
+    size_t nn;
+    int cur, it;
+    bool active, conv;
+    double err;
+  };
+  std::vector<Run> R(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    Run& u = R[r];
+    u.nn = (size_t)contours[r].n_c * contours[r].n_c;
+    const size_t one = align256(sizeof(double2) * u.nn);
+    char* p = runs + L.run_off[r];
+    u.g[0] = reinterpret_cast<double2*>(p);
+    u.g[1] = reinterpret_cast<double2*>(p + one);
+    u.s[0] = reinterpret_cast<double2*>(p + 2 * one);
+    u.s[1] = reinterpret_cast<double2*>(p + 3 * one);
+    u.cur = 0;
+    u.it = 1;
+    u.active = true;
+    u.conv = false;
+    u.err = INFINITY;
+    if (sigma_init_d && sigma_init_d[r])
+      NED_CUDA(cudaMemcpyAsync(u.s[0], sigma_init_d[r], sizeof(double2) * u.nn, cudaMemcpyDeviceToDevice, st));
+    else
+      NED_CUDA(cudaMemsetAsync(u.s[0], 0, sizeof(double2) * u.nn, st));
+    double* jr = j_d ? j_d[r] : nullptr;
+    if ((rc = lattice_run(contours[r], models[r], u.s[0], eps, ebar, wq, nq, prec, u.g[0], jr, nullptr, lat_ws, L.lat,
+                          st)))
+      return rc;
+  }
+  std::vector<double> eh(n_runs);
+  int active = max_iter > 1 ? n_runs : 0;
+  // one sweep: every active run takes one iteration; one host sync per sweep
+  while (active > 0) {
+    for (int r = 0; r < n_runs; ++r) {
+      Run& u = R[r];
+      if (!u.active) continue;
+      const int c = u.cur;
+      if ((rc = nedmft_impurity_update(&contours[r], &models[r], reinterpret_cast<const nedmft_c128*>(u.g[c]),
+                                       reinterpret_cast<const nedmft_c128*>(u.s[c]),
+                                       reinterpret_cast<nedmft_c128*>(u.s[1 - c]), nullptr, imp_ws, L.imp, st)))
+        return rc;
+      double* jr = j_d ? j_d[r] : nullptr;
+      if ((rc = lattice_run(contours[r], models[r], u.s[1 - c], eps, ebar, wq, nq, prec, u.g[1 - c], jr, nullptr,
+                            lat_ws, L.lat, st)))
+        return rc;
+      norm_pass1<<<kNormBlocks, 256, 0, st>>>(u.g[1 - c], u.g[c], u.nn, part);
+      NED_LAUNCH_CHECK("norm_pass1");
+      norm_pass2<<<1, 32, 0, st>>>(part, kNormBlocks, err_d + r);
+      NED_LAUNCH_CHECK("norm_pass2");
+    }
+    NED_CUDA(cudaMemcpyAsync(eh.data(), err_d, sizeof(double) * n_runs, cudaMemcpyDeviceToHost, st));
+    NED_CUDA(cudaStreamSynchronize(st));
+    if ((rc = nedmft_check_status(st))) return rc;
+    for (int r = 0; r < n_runs; ++r) {
+      Run& u = R[r];
+      if (!u.active) continue;
+      u.cur = 1 - u.cur;
+      ++u.it;
+      u.err = eh[r];
+      if (u.err < tol) u.conv = true;
+      if (u.conv || u.it >= max_iter) {
+        u.active = false;
+        --active;
+      }
+    }
+  }
+  bool all = true;
+  for (int r = 0; r < n_runs; ++r) {
+    const Run& u = R[r];
+    NED_CUDA(cudaMemcpyAsync(gloc_d[r], u.g[u.cur], sizeof(double2) * u.nn, cudaMemcpyDeviceToDevice, st));
+    NED_CUDA(cudaMemcpyAsync(sigma_d[r], u.s[u.cur], sizeof(double2) * u.nn, cudaMemcpyDeviceToDevice, st));
+    if (iters) iters[r] = u.it;
+    if (errs) errs[r] = u.err;
+    if (converged) converged[r] = u.conv ? 1 : 0;
+    all = all && u.conv;
+  }
+  NED_CUDA(cudaStreamSynchronize(st));
+  if ((rc = nedmft_check_status(st))) return rc;
+  return all ? NEDMFT_OK : NEDMFT_ENOTCONV;
+}

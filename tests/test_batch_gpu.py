@@ -1,0 +1,65 @@
+"""Several DMFT runs swept together (nedmft_dmft_solve_batch) against each run
+solved alone (nedmft_dmft_solve): the same kernels in the same order per run,
+so iterations agree and results agree to rounding; runs of different contour
+lengths and a run that stops at max_iter.  And the batch autotuner: it picks
+one of its candidates, later lattice steps use it, and the result does not
+depend on the batch size beyond rounding."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_0711_0999_gb300 import api
+from paper_0711_0999_gb300.build import build_library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    build_library()
+
+
+def rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_bf16"])
+def test_batch_matches_single_runs(prec):
+    grids = [api.contour_grid(-2, 4, 0.2, 10, 0.5), api.contour_grid(-2, 4, 0.2, 10, 0.5),
+             api.contour_grid(-2, 5, 0.125, 8, 0.5)]
+    models = [api.make_model(0.5, 1.0), api.make_model(1.0, 2.0), api.make_model(0.75, 0.5)]
+    sols = api.dmft_solve_batch(grids, models, 12, prec, tol=1e-8, max_iter=60)
+    for g, m, s in zip(grids, models, sols):
+        ref = api.dmft_solve(g, m, 12, prec, tol=1e-8, max_iter=60)
+        assert s.converged == ref.converged and s.iterations == ref.iterations
+        assert rel(s.gloc, ref.gloc) < 1e-12
+        assert rel(s.sigma, ref.sigma) < 1e-12
+        assert float((s.current - ref.current).abs().max()) < 1e-12
+        assert abs(s.error - ref.error) <= 1e-12 * max(1.0, ref.error)
+
+
+def test_batch_ragged_stop():
+    grids = [api.contour_grid(-2, 4, 0.2, 10, 0.5), api.contour_grid(-2, 3, 0.25, 6, 0.5)]
+    models = [api.make_model(0.5, 1.0), api.make_model(1.5, 1.0)]
+    sols = api.dmft_solve_batch(grids, models, 8, "fp64", tol=1e-14, max_iter=5)
+    for s in sols:
+        assert not s.converged and s.iterations == 5
+    ref = api.dmft_solve(grids[1], models[1], 8, "fp64", tol=1e-14, max_iter=5)
+    assert rel(sols[1].gloc, ref.gloc) < 1e-12
+
+
+def test_autotune_picks_a_candidate():
+    g = api.contour_grid(-2, 3, 0.05, 5.0, 0.25)  # N_c = 220
+    m = api.make_model(1.0, 1.0)
+    eps, ebar, wq = api.quadrature_grid(8)
+    sig = torch.zeros((g.n_c, g.n_c), dtype=torch.complex128, device="cuda")
+    before, _, _ = api.lattice_gloc(g, m, sig, eps, ebar, wq, precision="mixed_bf16")
+    best, ms = api.lattice_autotune(g, m, sig, eps, ebar, wq, "mixed_bf16", candidates=[16, 32, 64])
+    assert best in (16, 32, 64) and ms > 0
+    assert api.lattice_batch(g, 64, "mixed_bf16") == best
+    after, _, _ = api.lattice_gloc(g, m, sig, eps, ebar, wq, precision="mixed_bf16")
+    torch.cuda.synchronize()
+    assert rel(after, before) < 1e-12
