@@ -168,7 +168,7 @@ def load_peaks():
 # DRAM bytes of one Gauss-Jordan update launch (152 matrices at N_c = 1500), from
 # an ncu capture of the same kernel on 16 matrices scaled by 152 / 16; to be
 # re-taken whenever the update kernel changes
-UPDATE_TRAFFIC_BYTES = 715.6e6 * 152 / 16
+UPDATE_TRAFFIC_BYTES = 727.6e6 * 152 / 16
 
 
 def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str, clocks):
@@ -184,7 +184,7 @@ def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str, clo
         hpeak = peaks["hbm_gbs"]
         return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
                 "traffic": UPDATE_TRAFFIC_BYTES,
-                "traffic_note": "ncu dram__bytes_read + write of one update launch on 16 matrices (715 MB), "
+                "traffic_note": "ncu dram__bytes_read + write of one update launch on 16 matrices (728 MB), "
                                 "scaled by 152/16 to the benchmark launch",
                 "peak_source": f"sustained bf16 tensor rate / 3 (bf16x3 = three bf16 products per flop), {src}",
                 "hbm": {"achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
