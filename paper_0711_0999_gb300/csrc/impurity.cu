@@ -1,139 +1,8 @@
-// FP64 impurity step of the Falicov-Kimball DMFT loop and the dense
-// partial-pivoting inversion it uses.
+// FP64 impurity step of the Falicov-Kimball DMFT loop (the dense inversions
+// with partial pivoting live with the blocked Gauss-Jordan kernels).
 #include "lattice.cuh"
 
 namespace nedmft {
-
-// ------------------------------------------------------------------ Gauss-Jordan with partial pivoting
-
-// Workspace: colbuf (n), tmp matrix (n*n), pivot rows (n ints), inverse column map (n ints), pinv (1).
-size_t pivot_inverse_workspace(int n) {
-  return align256(sizeof(double2) * n) + align256(sizeof(double2) * (size_t)n * n) + align256(sizeof(int) * n) * 2 +
-         align256(sizeof(double2));
-}
-
-// Step k, part 1 (one CTA): pick the row p >= k with the largest |a_pk|, swap
-// rows k and p, save column k, scale row k by 1/a_kk (a_kk <- 1/a_kk).
-__global__ void __launch_bounds__(1024) piv_select_kernel(double2* __restrict__ a, int n, int k,
-                                                          double2* __restrict__ col, int* __restrict__ piv,
-                                                          double2* __restrict__ pinv_out, int* status) {
-  __shared__ double best_v[1024];
-  __shared__ int best_i[1024];
-  __shared__ double2 pinv_s;
-  double bv = -1.0;
-  int bi = k;
-  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-    double2 v = a[(size_t)i * n + k];
-    double m = v.x * v.x + v.y * v.y;
-    if (m > bv) { bv = m; bi = i; }
-  }
-  best_v[threadIdx.x] = bv;
-  best_i[threadIdx.x] = bi;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      double ov = best_v[threadIdx.x + s];
-      int oi = best_i[threadIdx.x + s];
-      if (ov > best_v[threadIdx.x] || (ov == best_v[threadIdx.x] && oi < best_i[threadIdx.x])) {
-        best_v[threadIdx.x] = ov;
-        best_i[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  const int p = best_i[0];
-  if (p != k) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double2 t = a[(size_t)k * n + j];
-      a[(size_t)k * n + j] = a[(size_t)p * n + j];
-      a[(size_t)p * n + j] = t;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 pv = a[(size_t)k * n + k];
-    double m = pv.x * pv.x + pv.y * pv.y;
-    if (!(m > 1e-280)) {
-      atomicCAS(status, 0, DS_SINGULAR);
-      pinv_s = make_double2(1e140, 0.0);
-    } else {
-      pinv_s = make_double2(pv.x / m, -pv.y / m);
-    }
-    piv[k] = p;
-    *pinv_out = pinv_s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = a[(size_t)i * n + k];
-  __syncthreads();
-  const double2 pinv = pinv_s;
-  for (int j = threadIdx.x; j < n; j += blockDim.x)
-    a[(size_t)k * n + j] = (j == k) ? pinv : cmul(a[(size_t)k * n + j], pinv);
-}
-
-// Step k, part 2: eliminate column k from every other row.
-__global__ void piv_eliminate_kernel(double2* __restrict__ a, int n, int k, const double2* __restrict__ col,
-                                     const double2* __restrict__ pinv_p) {
-  const double2 pinv = *pinv_p;
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / n), j = (int)(e % n);
-    if (i == k) continue;
-    double2 f = col[i];
-    if (j == k) {
-      double2 v = cmul(f, pinv);
-      a[e] = make_double2(-v.x, -v.y);
-    } else {
-      double2 r = a[(size_t)k * n + j];
-      double2 v = a[e];
-      v.x -= f.x * r.x - f.y * r.y;
-      v.y -= f.x * r.y + f.y * r.x;
-      a[e] = v;
-    }
-  }
-}
-
-// inv[idx] = j such that column j of A^-1 is column idx of the in-place result.
-__global__ void piv_colmap_kernel(int n, const int* __restrict__ piv, int* __restrict__ inv) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int j = 0; j < n; ++j) inv[j] = j;
-  for (int k = 0; k < n; ++k) {
-    int p = piv[k];
-    int t = inv[k]; inv[k] = inv[p]; inv[p] = t;
-  }
-}
-
-__global__ void piv_permute_kernel(const double2* __restrict__ x, int n, const int* __restrict__ inv,
-                                   double2* __restrict__ y) {
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / n), c = (int)(e % n);
-    y[(size_t)i * n + inv[c]] = x[e];
-  }
-}
-
-int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
-  char* p = static_cast<char*>(ws);
-  double2* col = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * n);
-  double2* tmp = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * (size_t)n * n);
-  int* piv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * n);
-  int* inv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * n);
-  double2* pinv = reinterpret_cast<double2*>(p);
-  const size_t total = (size_t)n * n;
-  int bx = (int)((total + 255) / 256);
-  if (bx > 152 * 8) bx = 152 * 8;
-  for (int k = 0; k < n; ++k) {
-    piv_select_kernel<<<1, 1024, 0, st>>>(a, n, k, col, piv, pinv, status);
-    NED_LAUNCH_CHECK("piv_select_kernel");
-    piv_eliminate_kernel<<<bx, 256, 0, st>>>(a, n, k, col, pinv);
-    NED_LAUNCH_CHECK("piv_eliminate_kernel");
-  }
-  piv_colmap_kernel<<<1, 1, 0, st>>>(n, piv, inv);
-  NED_LAUNCH_CHECK("piv_colmap_kernel");
-  piv_permute_kernel<<<bx, 256, 0, st>>>(a, n, inv, tmp);
-  NED_LAUNCH_CHECK("piv_permute_kernel");
-  NED_CUDA(cudaMemcpyAsync(a, tmp, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
-  return NEDMFT_OK;
-}
 
 // ------------------------------------------------------------------ impurity step
 

@@ -327,6 +327,254 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
 template int gj_blocked_simt<double>(double2*, int, int, int, double2*, double2*, double2*, int*, cudaStream_t);
 template int gj_blocked_simt<float>(float2*, int, int, int, float2*, float2*, float2*, int*, cudaStream_t);
 
+// ------------------------------------------------------------------ FP64 inversion with partial pivoting
+
+// Blocked Gauss-Jordan with partial pivoting for one dense matrix (the
+// impurity step).  Before each 32-column step the pivot rows of the block are
+// chosen by a tournament (as in communication-avoiding LU): chunks of
+// kTourRows candidate rows each run partial-pivoting LU on their part of the
+// block's columns and pass the 32 rows they pivot on to the next round, until
+// one chunk is left, whose pivot order is the block's.  The choice only
+// decides which rows to swap in; it runs in FP32 (a pivot need only be close
+// to the largest).  The rows are swapped in the FP64 matrix and the step
+// itself is the unpivoted blocked Gauss-Jordan step above.  The column
+// permutation of the result is undone at the end.
+constexpr int kTourRows = 256;
+constexpr int kTourNB = 32;
+
+// One tournament round.  Block c takes candidates c*kTourRows .. +kTourRows-1
+// (rows k0 + i of the matrix when `in` is NULL, else in[i]; -1 = no row) and
+// writes the <= 32 rows it pivots on (in pivot order, -1 padded) to
+// out[c*32 ..].  With final != 0 (one block) it turns the winners into the
+// swap sequence piv[k0 .. k0+31] (position k0 + j swaps with piv[k0 + j]).
+__global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restrict__ A, int np, int n, int k0,
+                                                         const int* __restrict__ in, int in_count,
+                                                         int* __restrict__ out, int final_round,
+                                                         int* __restrict__ piv, int* status) {
+  extern __shared__ float2 tp[];  // kTourRows x (kTourNB + 1)
+  __shared__ int gidx[kTourRows];
+  __shared__ float bv[kTourRows];
+  __shared__ int bi[kTourRows];
+  constexpr int LD = kTourNB + 1;
+  const int c = blockIdx.x, t = threadIdx.x;
+  const int i = c * kTourRows + t;
+  int row = -1;
+  if (i < in_count) row = in ? in[i] : k0 + i;
+  gidx[t] = row;
+  const int ncol = min(kTourNB, n - k0);
+  for (int j = 0; j < kTourNB; ++j) {
+    float2 v = make_float2(0.f, 0.f);
+    if (row >= 0 && j < ncol) {
+      const double2 z = A[(size_t)row * np + k0 + j];
+      v = make_float2((float)z.x, (float)z.y);
+    }
+    tp[t * LD + j] = v;
+  }
+  __syncthreads();
+  const int nrows = min(kTourRows, in_count - c * kTourRows);
+  const int steps = min(ncol, nrows);
+  for (int j = 0; j < steps; ++j) {
+    // largest |entry| of column j among local rows >= j (ties: lower local index)
+    float m = -1.f;
+    if (t >= j && t < nrows && gidx[t] >= 0) {
+      const float2 v = tp[t * LD + j];
+      m = v.x * v.x + v.y * v.y;
+    }
+    bv[t] = m;
+    bi[t] = t;
+    __syncthreads();
+    for (int s = kTourRows / 2; s > 0; s >>= 1) {
+      if (t < s) {
+        const float o = bv[t + s];
+        const int oi = bi[t + s];
+        if (o > bv[t] || (o == bv[t] && oi < bi[t])) {
+          bv[t] = o;
+          bi[t] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = bi[0];
+    // swap local rows j and p (one thread per column, then the index)
+    if (p != j && t < kTourNB) {
+      const float2 a = tp[j * LD + t];
+      tp[j * LD + t] = tp[p * LD + t];
+      tp[p * LD + t] = a;
+    }
+    __syncthreads();
+    if (t == 0 && p != j) {
+      const int g = gidx[j];
+      gidx[j] = gidx[p];
+      gidx[p] = g;
+    }
+    __syncthreads();
+    const float2 pv = tp[j * LD + j];
+    const float pm = pv.x * pv.x + pv.y * pv.y;
+    if (t > j && t < nrows && pm > 0.f) {
+      const float2 pinv = make_float2(pv.x / pm, -pv.y / pm);
+      const float2 a = tp[t * LD + j];
+      const float2 f = make_float2(a.x * pinv.x - a.y * pinv.y, a.x * pinv.y + a.y * pinv.x);
+      for (int cc = j + 1; cc < kTourNB; ++cc) {
+        const float2 r = tp[j * LD + cc];
+        float2 v = tp[t * LD + cc];
+        v.x -= f.x * r.x - f.y * r.y;
+        v.y -= f.x * r.y + f.y * r.x;
+        tp[t * LD + cc] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (t < kTourNB) out[c * kTourNB + t] = (t < steps) ? gidx[t] : -1;
+  if (final_round && t == 0) {
+    // winners -> swap sequence: position k0 + j takes the row now at the
+    // winner's position; `pos`/`row_at` track the (<= 64) touched positions
+    int pos_key[2 * kTourNB], pos_row[2 * kTourNB], used = 0;
+    auto row_at = [&](int q) {
+      for (int u = 0; u < used; ++u)
+        if (pos_key[u] == q) return pos_row[u];
+      return q;
+    };
+    auto set_at = [&](int q, int r) {
+      for (int u = 0; u < used; ++u)
+        if (pos_key[u] == q) { pos_row[u] = r; return; }
+      pos_key[used] = q;
+      pos_row[used] = r;
+      ++used;
+    };
+    for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
+      const int w = j < steps ? gidx[j] : -1;
+      int target = k0 + j;
+      if (w >= 0) {
+        // current position of row w: a touched position holding it, else w itself
+        int where = -1;
+        for (int u = 0; u < used; ++u)
+          if (pos_row[u] == w) { where = pos_key[u]; break; }
+        if (where < 0) where = (row_at(w) == w) ? w : -1;
+        if (where >= 0) target = where;
+      } else if (status) {
+        atomicCAS(status, 0, DS_SINGULAR);  // fewer nonzero candidates than columns
+      }
+      piv[k0 + j] = target;
+      if (target != k0 + j) {
+        const int ra = row_at(k0 + j), rb = row_at(target);
+        set_at(k0 + j, rb);
+        set_at(target, ra);
+      }
+    }
+  }
+}
+
+// Rows k0 + j <-> piv[k0 + j], j = 0 .. 31 in order; one thread per column.
+__global__ void apply_swaps_kernel(double2* __restrict__ A, int np, int n, int k0, const int* __restrict__ piv) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= np) return;
+  for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
+    const int p = piv[k0 + j];
+    if (p == k0 + j) continue;
+    const double2 a = A[(size_t)(k0 + j) * np + col];
+    A[(size_t)(k0 + j) * np + col] = A[(size_t)p * np + col];
+    A[(size_t)p * np + col] = a;
+  }
+}
+
+__global__ void pad_identity_kernel(const double2* __restrict__ a, int n, double2* __restrict__ ap, int np) {
+  const size_t total = (size_t)np * np;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / np), j = (int)(e % np);
+    ap[e] = (i < n && j < n) ? a[(size_t)i * n + j] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// inv[idx] = j such that column j of A^-1 is column idx of the in-place result
+// of the swapped matrix (the swaps applied in order).
+__global__ void swap_colmap_kernel(int n, const int* __restrict__ piv, int* __restrict__ inv) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int j = 0; j < n; ++j) inv[j] = j;
+  for (int k = 0; k < n; ++k) {
+    const int p = piv[k];
+    const int t = inv[k];
+    inv[k] = inv[p];
+    inv[p] = t;
+  }
+}
+
+__global__ void unpermute_kernel(const double2* __restrict__ x, int np, int n, const int* __restrict__ inv,
+                                 double2* __restrict__ y) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    y[(size_t)i * n + inv[c]] = x[(size_t)i * np + c];
+  }
+}
+
+size_t pivot_inverse_workspace(int n) {
+  const int np = ((n + 63) / 64) * 64;
+  const int nchunk = (n + kTourRows - 1) / kTourRows;
+  return align256(sizeof(double2) * (size_t)np * np) + align256(sizeof(double2) * kTourNB * kTourNB) +
+         2 * align256(sizeof(double2) * (size_t)kTourNB * np) + 2 * align256(sizeof(int) * (size_t)nchunk * kTourNB) +
+         2 * align256(sizeof(int) * (size_t)n);
+}
+
+int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
+  constexpr int NB = kTourNB;
+  const int np = ((n + 63) / 64) * 64;
+  const int nchunk = (n + kTourRows - 1) / kTourRows;
+  char* p = static_cast<char*>(ws);
+  double2* ap = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * (size_t)np * np);
+  double2* pbuf = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * NB * NB);
+  double2* rbuf = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * (size_t)NB * np);
+  double2* cbuf = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * (size_t)NB * np);
+  int* cand[2];
+  cand[0] = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)nchunk * NB);
+  cand[1] = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)nchunk * NB);
+  int* piv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
+  int* inv = reinterpret_cast<int*>(p);
+  const size_t total = (size_t)np * np;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 152 * 8) bx = 152 * 8;
+  pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np);
+  NED_LAUNCH_CHECK("pad_identity_kernel");
+  const size_t upd_smem = sizeof(double2) * (64 * (NB + 1) + NB * 64);
+  const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
+  static bool attr = false;
+  if (!attr) {
+    NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<double, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)upd_smem));
+    NED_CUDA(cudaFuncSetAttribute(tour_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tour_smem));
+    attr = true;
+  }
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    // tournament rounds over the rows k0 .. n-1
+    const int* in = nullptr;
+    int count = n - k0, buf = 0;
+    while (true) {
+      const int blocks = (count + kTourRows - 1) / kTourRows;
+      const int fin = blocks == 1;
+      tour_kernel<<<blocks, kTourRows, tour_smem, st>>>(ap, np, n, k0, in, count, cand[buf], fin, piv, status);
+      NED_LAUNCH_CHECK("tour_kernel");
+      if (fin) break;
+      in = cand[buf];
+      count = blocks * kTourNB;
+      buf ^= 1;
+    }
+    apply_swaps_kernel<<<(np + 255) / 256, 256, 0, st>>>(ap, np, n, k0, piv);
+    NED_LAUNCH_CHECK("apply_swaps_kernel");
+    gj_pivot_kernel<double, NB><<<1, 256, 0, st>>>(ap, np, k0, pbuf, status);
+    NED_LAUNCH_CHECK("gj_pivot_kernel");
+    gj_panels_kernel<double, NB><<<dim3(np / 32, 1), 256, 0, st>>>(ap, np, k0, pbuf, rbuf, cbuf);
+    NED_LAUNCH_CHECK("gj_panels_kernel");
+    gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf);
+    NED_LAUNCH_CHECK("gj_update_kernel");
+  }
+  swap_colmap_kernel<<<1, 1, 0, st>>>(n, piv, inv);
+  NED_LAUNCH_CHECK("swap_colmap_kernel");
+  int by = (int)(((size_t)n * n + 255) / 256);
+  if (by > 152 * 8) by = 152 * 8;
+  unpermute_kernel<<<by, 256, 0, st>>>(ap, np, n, inv, a);
+  NED_LAUNCH_CHECK("unpermute_kernel");
+  return NEDMFT_OK;
+}
+
 // ------------------------------------------------------------------ batched complex GEMM, CUDA cores
 
 // Cout[b] = A[b] (m x k) * B[b] (k x n), all row-major with the given leading
