@@ -531,6 +531,10 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
 
 // ------------------------------------------------------------------ epilogues
 
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat16 a, __nv_bfloat16 b) {
+  const __nv_bfloat162 v = __halves2bfloat162(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
 __device__ __forceinline__ uint4 shfl_xor_u4(uint4 v, int m) {
   return make_uint4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
                     __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
@@ -682,34 +686,40 @@ struct EpiRPack {
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 W)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
+  // row r of R, columns of the chunk: rows 2j, 2j+1 of the image at k = 2r,
+  // 2r+1; a quad of lanes (4 consecutive r) exchanges its values so that each
+  // lane writes whole 16-byte core-matrix rows (see EpiUpdate's Aᵀ panel)
   __device__ void operator()(int b, int mt, int nt, int r_tile, int c0, const float* v) const {
     __nv_bfloat16* base = img + b * bstride;
     const int r = mt * kTileRows + r_tile;  // row of R
-    const int n0 = nt * CfgGJ::kBn + c0;
+    const int l = r_tile & 3, rq = r - l;
+    const int j0 = (nt * CfgGJ::kBn + c0) >> 1;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int j = (n0 >> 1) + u;
-      const float re = v[2 * u], im = v[2 * u + 1];
-      __nv_bfloat16 rh, rl, ih, il, nh, nl;
-      split2(re, rh, rl);
-      split2(im, ih, il);
-      split2(-im, nh, nl);
-      const size_t o0 = img_offset(2 * j, 2 * r, kKtW);      // (re, -im)
-      const size_t o1 = img_offset(2 * j + 1, 2 * r, kKtW);  // (im, re)
-      *reinterpret_cast<__nv_bfloat162*>(base + o0) = __halves2bfloat162(rh, nh);
-      *reinterpret_cast<__nv_bfloat162*>(base + o1) = __halves2bfloat162(ih, rh);
-      *reinterpret_cast<__nv_bfloat162*>(base + slice + o0) = __halves2bfloat162(rl, nl);
-      *reinterpret_cast<__nv_bfloat162*>(base + slice + o1) = __halves2bfloat162(il, rl);
+    for (int jq = 0; jq < 4; ++jq) {
+      uint4 e[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int u = 4 * jq + p;
+        const float re = v[2 * u], im = v[2 * u + 1];
+        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        split2(re, rh, rl);
+        split2(im, ih, il);
+        split2(-im, nh, nl);
+        e[p] = make_uint4(bf2_bits(rh, nh), bf2_bits(ih, rh), bf2_bits(rl, nl), bf2_bits(il, rl));
+      }
+      quad_transpose4(e, l);
+      const int j = j0 + 4 * jq + l;
+      const size_t o0 = img_offset(2 * j, 2 * rq, kKtW), o1 = img_offset(2 * j + 1, 2 * rq, kKtW);
+      *reinterpret_cast<uint4*>(base + o0) = make_uint4(e[0].x, e[1].x, e[2].x, e[3].x);
+      *reinterpret_cast<uint4*>(base + o1) = make_uint4(e[0].y, e[1].y, e[2].y, e[3].y);
+      *reinterpret_cast<uint4*>(base + slice + o0) = make_uint4(e[0].z, e[1].z, e[2].z, e[3].z);
+      *reinterpret_cast<uint4*>(base + slice + o1) = make_uint4(e[0].w, e[1].w, e[2].w, e[3].w);
     }
   }
 };
 
 // ------------------------------------------------------------------ panel kernels (CUDA cores)
 
-__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat16 a, __nv_bfloat16 b) {
-  const __nv_bfloat162 v = __halves2bfloat162(a, b);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
 
 // P = inv(A_KK) (kNb x kNb, FP32, no pivoting -- the static row order makes
 // the pivots safe) written as the R-product's A operand: row r, k = 2c / 2c+1.
@@ -957,8 +967,10 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
   __nv_bfloat16* cd = cimg + b * cstride;
   __nv_bfloat16* td = timg + b * tstride;
   for (int e = threadIdx.x; e < 128 * G; e += blockDim.x) {
-    {  // C'[i][c4 .. c4+3]
-      const int i = base + e / G, c4 = 4 * (e % G);
+    {  // C'[i][c4 .. c4+3]; a warp covers 8 rows x 4 cores (4 contiguous 128-byte core matrices)
+      const int grp = e >> 5;
+      const int i = base + (grp & 15) * 8 + (e & 7);
+      const int c4 = 4 * ((grp >> 4) * 4 + ((e >> 3) & 3));
       const bool in = (i >= k0 && i < k0 + W);
       uint32_t hi[4], lo[4];
 #pragma unroll
