@@ -1791,19 +1791,36 @@ __global__ void __launch_bounds__(256) reduce_refined_kernel(ContourDev c, Model
       const size_t e = (size_t)i * c.n + j;
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
       const int j0 = j, j1 = (j == 0 ? c.n - 1 : j - 1);
-      for (int b = 0; b < nb; ++b) {
-        const size_t off = b * mat + (size_t)i * np + (shf[b] ? j1 : j0);
-        const float2 x = X[off];
-        const float h = wh[b], l = wl[b];
-        float px = h * x.x, ex = fmaf(h, x.x, -px) + l * x.x;
-        float py = h * x.y, ey = fmaf(h, x.y, -py) + l * x.y;
-        if (rf[b]) {
-          const float2 d = dX[off];
-          ex += h * d.x;
-          ey += h * d.y;
+      // eight matrices' loads in flight at a time; the sum still runs over b in order
+      constexpr int U = 8;
+      for (int b0 = 0; b0 < nb; b0 += U) {
+        float2 xs[U], ds[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int b = b0 + u;
+          xs[u] = make_float2(0.f, 0.f);
+          ds[u] = make_float2(0.f, 0.f);
+          if (b < nb) {
+            const size_t off = b * mat + (size_t)i * np + (shf[b] ? j1 : j0);
+            xs[u] = X[off];
+            if (rf[b]) ds[u] = dX[off];
+          }
         }
-        df_add(rh, rl, px, ex);
-        df_add(ih, il, py, ey);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int b = b0 + u;
+          if (b >= nb) break;
+          const float2 x = xs[u];
+          const float h = wh[b], l = wl[b];
+          float px = h * x.x, ex = fmaf(h, x.x, -px) + l * x.x;
+          float py = h * x.y, ey = fmaf(h, x.y, -py) + l * x.y;
+          if (rf[b]) {
+            ex += h * ds[u].x;
+            ey += h * ds[u].y;
+          }
+          df_add(rh, rl, px, ex);
+          df_add(ih, il, py, ey);
+        }
       }
       double2 acc = first ? make_double2(0.0, 0.0) : gloc[e];
       acc.x += (double)rh + (double)rl;
