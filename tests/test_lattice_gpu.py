@@ -213,6 +213,31 @@ def test_impurity_update_matches_oracle():
     assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
 
 
+@pytest.mark.parametrize("args", [(-2, 4, 0.2, 10, 0.5), (-2, 3, 0.05, 5.0, 0.25)])
+def test_impurity_update_needs_pivoting(args):
+    # G_loc = (cyclic row shift)(I + 0.3 R) with its diagonal set to zero:
+    # every pivot of an elimination without row exchanges is 0 at the first
+    # step, so the inversions need them; N_c = 80 and 220 (ragged last blocks)
+    c = O.contour_grid(*args)
+    g = api.contour_grid(*args)
+    n = c.n_c
+    rng = np.random.default_rng(7)
+    base = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    gl = np.roll(base, 1, axis=0).astype(np.complex128)
+    np.fill_diagonal(gl, 0.0)
+    sig = workload_sigma(c.t, c.w, 1.0, seed=3)
+    mo, mc = O.Model(U=1.0, E=1.0), api.make_model(1.0, 1.0)
+    s_ref, gi_ref = O.impurity_update(c, mo, gl, sig)
+    s_new, gimp = api.impurity_update(g, mc, torch.as_tensor(gl, device="cuda"), torch.as_tensor(sig, device="cuda"),
+                                      want_gimp=True)
+    torch.cuda.synchronize()
+    api.check_status()
+    w = c.w
+    sw = lambda s: w[:, None] * s * w[None, :]
+    assert rel(sw(s_new.cpu().numpy()), sw(s_ref)) < 1e-10
+    assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
+
+
 def test_dmft_solve_small_config_matches_oracle():
     args = (-2, 4, 0.2, 10, 0.5)
     c = O.contour_grid(*args)
