@@ -310,7 +310,7 @@ def main():
     import torch
 
     from paper_0711_0999_gb300 import _native as N
-    from paper_0711_0999_gb300 import api
+    from paper_0711_0999_gb300 import api, sharding
     from paper_0711_0999_gb300.synth import workload_sigma
 
     # the oracle pool starts before the first GPU call
@@ -383,11 +383,7 @@ def main():
     lib.nedmft_instrument(0, 0)
     clk = clocks.stop()
     api.check_status()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = sharding.max_over_ranks(ms, dev)  # the job's time is its slowest rank's
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     n = grid.n_c
@@ -423,12 +419,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize(dev)
         barrier()
-        e_s = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
+        e_s = sharding.max_over_ranks(time.perf_counter() - t0, dev)
         h2d = sig_h.numel() * 16 + 3 * nq * 8
         d2h = g_h.numel() * 16 + 2 * grid.n_t * 8
         e2e = {"value": world * args.steps / e_s, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
