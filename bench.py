@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = 2 x cores)")
+    ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = 5 x cores)")
     ap.add_argument("--n-quad", type=int, default=0, help="override the quadrature size (profiling runs only)")
     ap.add_argument("--tts", action="store_true",
                     help="time to a converged solution: mixed + learned warm start vs mixed zero start vs FP64")
@@ -79,7 +79,7 @@ def oracle_sample(n_points: int | None = None):
 
     W = WORKLOAD
     cores = os.cpu_count() or 1
-    npts = n_points or 2 * cores
+    npts = n_points or 5 * cores  # about 12 s of CPU work on 16 cores
     c = O.contour_grid(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"])
     sigma = workload_sigma(c.t, c.w, W["U"])
     eps, ebar, _ = O.quadrature_points(W["n_quad"])
