@@ -183,31 +183,13 @@ __device__ __forceinline__ void umma_gemm_body(const GemmParams& p, const Epi& e
   if (threadIdx.x == 0 && *abort_flag && p.status) atomicCAS(p.status, 0, DS_TIMEOUT);
 }
 
-template <class C, class Pairs, class Epi>
-__global__ void __launch_bounds__(192, 1) umma_gemm_kernel(GemmParams p, Epi epi) {
-  umma_gemm_body<C, Pairs, Epi>(p, epi);
-}
-
-// the same GEMM, skipping the matrices whose flag is 0
+// One tile per CTA (non-persistent), skipping the matrices whose flag is 0.
 template <class C, class Pairs, class Epi>
 __global__ void __launch_bounds__(192, 1) umma_gemm_flag_kernel(GemmParams p, Epi epi, const int* flags, int q0) {
   if (!flags[q0 + blockIdx.z]) return;
   umma_gemm_body<C, Pairs, Epi>(p, epi);
 }
 
-template <class C, class Pairs, class Epi>
-int launch_gemm(const GemmParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    NED_CUDA(cudaFuncSetAttribute(umma_gemm_kernel<C, Pairs, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  C::kSmem));
-    attr = true;
-  }
-  dim3 grid(n_tiles, m_tiles, batch);
-  umma_gemm_kernel<C, Pairs, Epi><<<grid, 192, C::kSmem, st>>>(p, epi);
-  NED_LAUNCH_CHECK("umma_gemm_kernel");
-  return NEDMFT_OK;
-}
 
 using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (192 KB)
 
@@ -1841,16 +1823,34 @@ __global__ void reduce_refined_current_kernel(ContourDev c, ModelDev mo, const d
   const double t = t_re(c, mm);
   const int jcol = 2 * c.nt - mm;
   const size_t mat = (size_t)np * np;
+  // ebar_q(t) = ebar cos(Et) + eps sin(Et) for t > 0 (ebar before): the
+  // trigonometric factors are the same for every point
+  double sn = 0.0, cs = 1.0;
+  if (t > 0.0) sincos(mo.E * t, &sn, &cs);
   double2 acc = first ? make_double2(0.0, 0.0) : jacc[mm];
-  for (int b = 0; b < nb; ++b) {
-    const int q = q0 + b;
-    const double eps = eps_d[q];
-    const size_t off = b * mat + (size_t)mm * np + unshift_col(jcol, c.n, shifted_point(mo, eps));
-    double2 v = to_d(X[off]);
-    if (flags[q]) v = cadd(v, to_d(dX[off]));
-    const double w = wq_d[q] * ebar_at(t, eps, ebar_d[q], mo.E);
-    acc.x = fma(w, v.x, acc.x);
-    acc.y = fma(w, v.y, acc.y);
+  constexpr int U = 8;  // loads of eight points in flight; the sum runs over b in order
+  for (int b0 = 0; b0 < nb; b0 += U) {
+    double2 vs[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int b = b0 + u;
+      vs[u] = make_double2(0.0, 0.0);
+      if (b < nb) {
+        const int q = q0 + b;
+        const size_t off = b * mat + (size_t)mm * np + unshift_col(jcol, c.n, shifted_point(mo, eps_d[q]));
+        vs[u] = to_d(X[off]);
+        if (flags[q]) vs[u] = cadd(vs[u], to_d(dX[off]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int b = b0 + u;
+      if (b >= nb) break;
+      const int q = q0 + b;
+      const double w = wq_d[q] * (ebar_d[q] * cs + eps_d[q] * sn);
+      acc.x = fma(w, vs[u].x, acc.x);
+      acc.y = fma(w, vs[u].y, acc.y);
+    }
   }
   jacc[mm] = acc;
 }
