@@ -1206,20 +1206,10 @@ namespace {
 
 constexpr int kOzS = 4;           // slices per operand
 constexpr int kOzBits = 7;        // bits per slice
-constexpr int kOzPairs = 10;      // slice pairs with a + b <= kOzS - 1
 constexpr int kOzBn = 64;         // output columns per tile (32 complex)
 constexpr int kOzChunkKt = 16;    // K tiles per exact chunk (1024)
 constexpr int kRedMaxBatch = 512;
 constexpr double kRefineTail = 1e-3;
-
-__device__ __forceinline__ void oz_pair(int q, int& a, int& b, int& d) {
-  // d = a + b (slice order); the accumulator of order d
-  const int ta[kOzPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-  const int tb[kOzPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-  a = ta[q];
-  b = tb[q];
-  d = a + b;
-}
 
 // double-float helpers (hi + lo, |lo| <= ulp(hi)/2 after renormalisation)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -1517,11 +1507,15 @@ constexpr int kOzStageBytes = kOzS * (kOzHalfA + kOzHalfB);  // 48 KB
 constexpr int kOzStages = 4;
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 
-// Persistent: the units (refined matrix, m tile, n tile), m fastest, are
-// dealt round-robin to the CTAs; consecutive units share the B tile and all
-// share A (S_d), which stays in L2.  Chunks of kOzChunkKt K tiles alternate
-// between two TMEM buffers of kOzS accumulators of kOzBn columns across units,
-// so the epilogue drains (and finishes a unit) while the next chunk is multiplied.
+// Persistent, in clusters of two CTAs: the units (refined matrix, m tile, pair
+// of n tiles), m fastest, are dealt round-robin to the clusters; CTA r of a
+// cluster takes n tile 2 j + r, so both multiply the same rows of S_d: each
+// loads half of the A slices, multicast to both, and its own B half tile, and a
+// stage is refilled only when both CTAs' products have released it.
+// Consecutive units share the B tile and all share A (S_d), which stays in L2.
+// Chunks of kOzChunkKt K tiles alternate between two TMEM buffers of kOzS
+// accumulators of kOzBn columns across units, so the epilogue drains (and
+// finishes a unit) while the next chunk is multiplied.
 __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -1534,8 +1528,10 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
   __shared__ int refined[kRedMaxBatch];
   __shared__ int n_refined;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tiles = p.np / kTileRows, n_tiles = 2 * p.np / kOzBn;
-  const int per = m_tiles * n_tiles;
+  const int m_tiles = p.np / kTileRows, n_pairs = p.np / kOzBn;  // 2 np / kOzBn n tiles, in pairs
+  const int per = m_tiles * n_pairs;
+  const int rank = (int)cluster_ctarank();
+  constexpr uint16_t kBoth = 3;
   const int kh = 2 * p.kt;                  // half tiles per unit
   const int hc = 2 * kOzChunkKt;            // half tiles per chunk
   const int nchunks = (kh + hc - 1) / hc;   // chunks per unit
@@ -1543,7 +1539,7 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
   if (threadIdx.x == 0) {
     for (int s = 0; s < kOzStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], 2);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
@@ -1559,21 +1555,22 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
   if (warp == 1) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int units = n_refined * per;
-  const int G = gridDim.x;
+  const int G = gridDim.x / 2, cl = blockIdx.x / 2;
 
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < units && ok; u += G) {
+      for (int u = cl; u < units && ok; u += G) {
         const int bidx = refined[u / per], rem = u % per;
-        const int mt = rem % m_tiles, nt = rem / m_tiles;
+        const int mt = rem % m_tiles, ntp = rem / m_tiles;
         const long long a0 = (long long)mt * p.kt;
-        const long long b0 = bidx * p.b_batch + (long long)(nt >> 1) * p.kt;
-        const int rg = 8 * (nt & 1);  // B rows nt*64 .. +63: row groups 8 (nt & 1) .. +7 of tile nt >> 1
+        const long long b0 = bidx * p.b_batch + (long long)ntp * p.kt;
+        const int rg = 8 * rank;  // B rows (2 ntp + rank) * 64 .. +63: row groups 8 rank .. +7 of tile ntp
         for (int h = 0; h < kh; ++h, ++it) {
           const int s = it % kOzStages;
           const uint32_t ph = (it / kOzStages) & 1;
@@ -1581,8 +1578,8 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
           unsigned char* st = smem + s * kOzStageBytes;
           const int kt = h >> 1, kc = 4 * (h & 1);
           mbar_arrive_expect_tx(&full[s], kOzStageBytes);
-          for (int sl = 0; sl < kOzS; ++sl)
-            tma_load_4d(&p.a_map, st + sl * kOzHalfA, 0, kc, 0, (int)(a0 + sl * p.a_slice + kt), &full[s]);
+          for (int sl = rank * (kOzS / 2); sl < (rank + 1) * (kOzS / 2); ++sl)
+            tma_load_4d_mc(&p.a_map, st + sl * kOzHalfA, 0, kc, 0, (int)(a0 + sl * p.a_slice + kt), &full[s], kBoth);
           for (int sl = 0; sl < kOzS; ++sl)
             tma_load_4d(&p.b_map, st + kOzS * kOzHalfA + sl * kOzHalfB, 0, kc, rg, (int)(b0 + sl * p.b_slice + kt),
                         &full[s]);
@@ -1597,10 +1594,9 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(128, kOzBn);
       bool ok = true;
       int it = 0, cg = 0;  // stage uses, chunks (across units)
-      for (int u = blockIdx.x; u < units && ok; u += G) {
+      for (int u = cl; u < units && ok; u += G) {
         for (int h = 0; h < kh && ok; ++h, ++it) {
           const bool first = (h % hc) == 0;
           const int buf = cg & 1;
@@ -1612,20 +1608,21 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
           if (!mbar_wait(&full[s], (it / kOzStages) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + s * kOzStageBytes);
+          // The B slices lie back to back (64 rows each, 8-row groups 512 B
+          // apart), so B_0 .. B_{kOzS-1-a} form one operand of (kOzS - a) * 64
+          // rows: one MMA per A slice a writes A_a B_b to accumulator
+          // d = a + b (columns d * kOzBn), and a = 0 opens every order.
 #pragma unroll
           for (int kk = 0; kk < kTileK / 32; ++kk) {
+            const uint32_t b_addr = st + kOzS * kOzHalfA + kk * 256;
 #pragma unroll
-            for (int q = 0; q < kOzPairs; ++q) {
-              int a, b, d;
-              oz_pair(q, a, b, d);
-              const bool first_of_d = (q == 0 || q == 1 || q == 3 || q == 6);
+            for (int a = 0; a < kOzS; ++a) {
               const uint32_t a_addr = st + a * kOzHalfA + kk * 256;
-              const uint32_t b_addr = st + kOzS * kOzHalfA + b * kOzHalfB + kk * 256;
-              mma_bf16(tmem + buf * 256 + d * kOzBn, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc,
-                       (first && kk == 0 && first_of_d) ? 0u : 1u);
+              mma_bf16(tmem + buf * 256 + a * kOzBn, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512),
+                       idesc_bf16(128, (kOzS - a) * kOzBn), (first && kk == 0 && a == 0) ? 0u : 1u);
             }
           }
-          mma_commit(&empty[s]);
+          mma_commit_mc(&empty[s], kBoth);
           if ((h % hc) == hc - 1 || h == kh - 1) {
             mma_commit(&acc_full[buf]);
             ++cg;
@@ -1642,13 +1639,55 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
     const int row = q * 32 + lane;
     bool ok = true;
     int cg = 0;
-    for (int u = blockIdx.x; u < units && ok; u += G) {
+    for (int u = cl; u < units && ok; u += G) {
       const int bidx = refined[u / per], rem = u % per;
-      const int mt = rem % m_tiles, nt = rem / m_tiles;
+      const int mt = rem % m_tiles, nt = 2 * (rem / m_tiles) + rank;
       const int i = mt * kTileRows + row;  // output row of S_d X'
+      const int n = p.c.n, np = p.np;
+      const bool sh = shifted_point(p.m, p.eps[p.q0 + bidx]);
+      const int r = (i < n && sh) ? (i == 0 ? n - 1 : i - 1) : i;  // row of R' fed by row i
+      const int ei = p.a_exp[i];
+      const int* xe = p.b_exp + (size_t)bidx * np;
+      const int j0 = nt * (kOzBn / 2);
+      // The sums start from T - (B - S_sp) X' at (i, j) (double-float, in the
+      // accumulator's units 2^(e_i + e_j)), so the reads of X' rows (16-byte
+      // vectors) overlap the products of the unit's first chunk.
       float hs[kOzBn], ls[kOzBn];
+      {
+        const float2* x = p.X + (size_t)bidx * np * np;
+        const float4* cf = p.coef + (size_t)bidx * np * 3;
+        // the diagonal, and one off-diagonal entry: the subdiagonal (row i - 1)
+        // for 1 <= i < n, the corner (row n - 1) for i = 0, none beyond n
+        const float4 cd = cf[3 * i], co = i == 0 ? cf[2] : cf[3 * i + 1];
+        const float4* xd = reinterpret_cast<const float4*>(x + (size_t)i * np + j0);
+        const int io = i == 0 ? n - 1 : i - 1;
+        const float4* xo = i < n ? reinterpret_cast<const float4*>(x + (size_t)io * np + j0) : nullptr;
 #pragma unroll
-      for (int e = 0; e < kOzBn; ++e) { hs[e] = 0.f; ls[e] = 0.f; }
+        for (int v = 0; v < kOzBn / 4; ++v) {  // two complex columns per vector
+          const float4 zd = xd[v];
+          const float4 zo = xo ? xo[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int uu = 2 * v + h, j = j0 + uu;
+            float tr_h = 0.f, tr_l = 0.f, ti_h = 0.f, ti_l = 0.f;
+            auto sub_prod = [&](float4 co, float xr, float xi) {
+              float hh, ll;
+              df_mul_f(co.x, co.y, xr, hh, ll); df_add(tr_h, tr_l, -hh, -ll);  // - c_re x_re
+              df_mul_f(co.z, co.w, xi, hh, ll); df_add(tr_h, tr_l, hh, ll);    // + c_im x_im
+              df_mul_f(co.x, co.y, xi, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_re x_im
+              df_mul_f(co.z, co.w, xr, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_im x_re
+            };
+            sub_prod(cd, h ? zd.z : zd.x, h ? zd.w : zd.y);
+            if (xo) sub_prod(co, h ? zo.z : zo.x, h ? zo.w : zo.y);
+            if (r == j) df_add(tr_h, tr_l, 1.0f, 0.0f);
+            const int sc = -(ei + xe[j]);
+            hs[2 * uu] = ldexpf(tr_h, sc);
+            ls[2 * uu] = ldexpf(tr_l, sc);
+            hs[2 * uu + 1] = ldexpf(ti_h, sc);
+            ls[2 * uu + 1] = ldexpf(ti_l, sc);
+          }
+        }
+      }
       for (int ch = 0; ch < nchunks; ++ch, ++cg) {
         const int buf = cg & 1;
         if (!mbar_wait(&acc_full[buf], (cg >> 1) & 1, abort_flag)) { ok = false; break; }
@@ -1673,35 +1712,14 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
         mbar_arrive(&acc_empty[buf]);
       }
       if (!ok || *abort_flag) break;
-      const int n = p.c.n, np = p.np;
-      const bool sh = shifted_point(p.m, p.eps[p.q0 + bidx]);
-      const int r = (i < n && sh) ? (i == 0 ? n - 1 : i - 1) : i;  // row of R' fed by row i
-      const float2* x = p.X + (size_t)bidx * np * np;
-      const float4* cf = p.coef + (size_t)bidx * np * 3;
-      const float4 cd = cf[3 * i], cs = cf[3 * i + 1], cc = cf[3 * i + 2];
-      const int ei = p.a_exp[i];
-      const int* xe = p.b_exp + (size_t)bidx * np;
       __nv_bfloat16* ri = p.rimg + bidx * p.r_batch;
       const int kt = 2 * np / kTileK;
-      const int j0 = nt * (kOzBn / 2);
 #pragma unroll
       for (int uu = 0; uu < kOzBn / 2; ++uu) {
         const int j = j0 + uu;
         const int sc = ei + xe[j];
-        float tr_h = ldexpf(hs[2 * uu], sc), tr_l = ldexpf(ls[2 * uu], sc);
-        float ti_h = ldexpf(hs[2 * uu + 1], sc), ti_l = ldexpf(ls[2 * uu + 1], sc);
-        // T - (B - S_sp) X' at (i, j), double-float
-        auto sub_prod = [&](float4 co, float2 xv) {
-          float hh, ll;
-          df_mul_f(co.x, co.y, xv.x, hh, ll); df_add(tr_h, tr_l, -hh, -ll);  // - c_re x_re
-          df_mul_f(co.z, co.w, xv.y, hh, ll); df_add(tr_h, tr_l, hh, ll);    // + c_im x_im
-          df_mul_f(co.x, co.y, xv.y, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_re x_im
-          df_mul_f(co.z, co.w, xv.x, hh, ll); df_add(ti_h, ti_l, -hh, -ll);  // - c_im x_re
-        };
-        sub_prod(cd, x[(size_t)i * np + j]);
-        if (i >= 1 && i < n) sub_prod(cs, x[(size_t)(i - 1) * np + j]);
-        if (i == 0) sub_prod(cc, x[(size_t)(n - 1) * np + j]);
-        if (r == j) df_add(tr_h, tr_l, 1.0f, 0.0f);
+        const float tr_h = ldexpf(hs[2 * uu], sc), tr_l = ldexpf(ls[2 * uu], sc);
+        const float ti_h = ldexpf(hs[2 * uu + 1], sc), ti_l = ldexpf(ls[2 * uu + 1], sc);
         const float re = tr_h + tr_l, im = ti_h + ti_l;
         __nv_bfloat16 rh, rl, ih, il, nh, nl;
         split2(re, rh, rl);
@@ -1718,14 +1736,19 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
   }
   __syncthreads();
   if (warp == 1) {
-    // every MMA of this CTA has completed before the TMEM is released
-    const int chunks = ((units - (int)blockIdx.x + G - 1) / G > 0 ? (units - (int)blockIdx.x + G - 1) / G : 0) * nchunks;
+    // every MMA of this CTA (and so its releases of the peer's stages) has
+    // completed before the cluster is left and the TMEM is released
+    const int mine = (units - cl + G - 1) / G > 0 ? (units - cl + G - 1) / G : 0;
+    const int chunks = mine * nchunks;
     for (int s = 0; s < 2 && s < chunks; ++s) {
       const int last = ((chunks - 1 - s) / 2) * 2 + s;  // last chunk that used buffer s
       const uint64_t t0 = global_ns();
       while (!mbar_test(&acc_full[s], (last >> 1) & 1) && global_ns() - t0 < kWaitNs) {
       }
     }
+  }
+  cluster_sync();  // no multicast or release into a CTA that has left
+  if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -1967,18 +1990,27 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
     p.rimg = rimg; p.r_batch = 2 * rs; p.r_slice = rs;
     p.c = c; p.m = m; p.eps = eps; p.q0 = q0; p.nb = nb; p.np = np; p.kt = 2 * np / kTileK; p.status = status;
     if (nb > kRedMaxBatch) return set_error(NEDMFT_EINVAL, "residual: batch %d > %d", nb, kRedMaxBatch);
-    static bool attr = false;
-    if (!attr) {
+    // clusters of two CTAs sharing the A slices; as many clusters as fit at once
+    static int max_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = kOzSmem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (!max_clusters) {
       NED_CUDA(cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
-      attr = true;
+      cfg.gridDim = dim3(2);
+      NED_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, oz_residual_kernel, &cfg));
+      if (max_clusters < 1) return set_error(NEDMFT_ECUDA, "residual: no cluster of 2 fits on this device");
     }
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      NED_CUDA(cudaGetDevice(&dev));
-      NED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    oz_residual_kernel<<<sms, 192, kOzSmem, st>>>(p);
+    cfg.gridDim = dim3(2 * max_clusters);
+    NED_CUDA(cudaLaunchKernelEx(&cfg, oz_residual_kernel, p));
     NED_LAUNCH_CHECK("oz_residual_kernel");
   }
   {  // dX' = X' R' (bf16x3), refined points only
