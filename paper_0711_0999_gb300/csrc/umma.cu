@@ -710,7 +710,8 @@ struct EpiRPack {
 //   B11 <- P1 = inv(A11);  B12 <- P1 A12;  B22 <- A22 - A21 B12;  B21 <- -A21 P1;
 //   B22 <- X22 = inv(B22); V = -B12 X22;  B21 <- X22 B21;  B11 <- P1 + V B21(old);  B12 <- V,
 // the two 64 x 64 inversions unblocked (one barrier per pivot, 2 x 2 complex
-// entries per thread), the products by all 1024 threads (1 x 4 outputs each).
+// entries per thread), the products by two halves of 512 threads (4 x 2
+// outputs each).
 constexpr int kPivH = kNb / 2;
 constexpr size_t kPivSmem = (size_t)(kNb * kNb + kPivH * kPivH) * sizeof(float2);  // 160 KB
 
@@ -781,40 +782,49 @@ __device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
     for (int j = 0; j < 2; ++j) M[(o + rr + i) * kNb + o + cc + j] = a[i][j];
 }
 
-// acc[q] = sum_k X[i][k] Y[k][j0 + q] over 64 x 64 blocks (row strides ldx, ldy),
-// i = t / 16, j0 = 4 (t % 16)
-__device__ __forceinline__ void piv_gemm64(const float2* X, int ldx, const float2* Y, int ldy, float2* acc) {
-  const int t = threadIdx.x;
-  const int i = t >> 4, j0 = 4 * (t & 15);
+// acc[a][c] = sum_{k0 <= k < k0 + kn} X[i0 + a][k] Y[k][j0 + c] (a < 4, c < 2)
+// for the 4 x 2 block of thread s (0 .. 511) of a 64 x 64 product (row
+// strides ldx, ldy): i0 = 4 (s / 32), j0 = 2 (s % 32), so a warp reads one X
+// entry per row (a broadcast) and one 512-byte row of Y per k.
+__device__ __forceinline__ void piv_mm(const float2* X, int ldx, const float2* Y, int ldy, int s, int k0, int kn,
+                                       float2 (&acc)[4][2]) {
+  const int i0 = 4 * (s >> 5), j0 = 2 * (s & 31);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-#pragma unroll 8
-  for (int k = 0; k < kPivH; ++k) {
-    const float2 x = X[i * ldx + k];
-    const float4 y01 = *reinterpret_cast<const float4*>(Y + k * ldy + j0);
-    const float4 y23 = *reinterpret_cast<const float4*>(Y + k * ldy + j0 + 2);
-    const float2 y[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w), make_float2(y23.x, y23.y),
-                         make_float2(y23.z, y23.w)};
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int k = k0; k < k0 + kn; ++k) {
+    const float4 y = *reinterpret_cast<const float4*>(Y + k * ldy + j0);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      acc[q].x += x.x * y[q].x - x.y * y[q].y;
-      acc[q].y += x.x * y[q].y + x.y * y[q].x;
+    for (int a = 0; a < 4; ++a) {
+      const float2 x = X[(i0 + a) * ldx + k];
+      acc[a][0].x += x.x * y.x - x.y * y.y;
+      acc[a][0].y += x.x * y.y + x.y * y.x;
+      acc[a][1].x += x.x * y.z - x.y * y.w;
+      acc[a][1].y += x.x * y.w + x.y * y.z;
     }
   }
 }
-__device__ __forceinline__ void piv_put(float2* Z, int ldz, const float2* v) {
-  const int t = threadIdx.x;
-  const int i = t >> 4, j0 = 4 * (t & 15);
-  *reinterpret_cast<float4*>(Z + i * ldz + j0) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-  *reinterpret_cast<float4*>(Z + i * ldz + j0 + 2) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+__device__ __forceinline__ void piv_put(float2* Z, int ldz, int s, const float2 (&v)[4][2]) {
+  const int i0 = 4 * (s >> 5), j0 = 2 * (s & 31);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    *reinterpret_cast<float4*>(Z + (i0 + a) * ldz + j0) = make_float4(v[a][0].x, v[a][0].y, v[a][1].x, v[a][1].y);
 }
-__device__ __forceinline__ void piv_get(const float2* Z, int ldz, float2* v) {
-  const int t = threadIdx.x;
-  const int i = t >> 4, j0 = 4 * (t & 15);
-  const float4 a = *reinterpret_cast<const float4*>(Z + i * ldz + j0);
-  const float4 b = *reinterpret_cast<const float4*>(Z + i * ldz + j0 + 2);
-  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
-  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+// v += sign * Z (the thread's 4 x 2 block)
+__device__ __forceinline__ void piv_acc(const float2* Z, int ldz, int s, float sign, float2 (&v)[4][2]) {
+  const int i0 = 4 * (s >> 5), j0 = 2 * (s & 31);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 z = *reinterpret_cast<const float4*>(Z + (i0 + a) * ldz + j0);
+    v[a][0].x += sign * z.x; v[a][0].y += sign * z.y;
+    v[a][1].x += sign * z.z; v[a][1].y += sign * z.w;
+  }
+}
+__device__ __forceinline__ void piv_neg(float2 (&v)[4][2]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) v[a][c] = make_float2(-v[a][c].x, -v[a][c].y);
 }
 
 __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
@@ -838,44 +848,52 @@ __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __res
   }
   if (t == 0) sh.bad = 0;
   __syncthreads();
-  float2 u[4], w[4];
+  // two halves of 512 threads: a product alone is split along K (the upper
+  // half's partial sums pass through T), two independent products run side by side
+  const int half = t >> 9, s = t & 511;
+  float2 u[4][2];
   piv_gj64(M, 0, sh);  // B11 <- P1
   __syncthreads();
-  piv_gemm64(B11, kNb, B12, kNb, u);  // P1 A12
+  piv_mm(B11, kNb, B12, kNb, s, 32 * half, 32, u);  // P1 A12
+  if (half) piv_put(T, kPivH, s, u);
   __syncthreads();
-  piv_put(B12, kNb, u);
+  if (!half) {
+    piv_acc(T, kPivH, s, 1.f, u);
+    piv_put(B12, kNb, s, u);  // B12 <- P1 A12
+  }
   __syncthreads();
-  piv_gemm64(B21, kNb, B12, kNb, u);  // A21 B12
-  piv_gemm64(B21, kNb, B11, kNb, w);  // A21 P1
-  {
-    float2 z[4];
-    piv_get(B22, kNb, z);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { z[q].x -= u[q].x; z[q].y -= u[q].y; w[q].x = -w[q].x; w[q].y = -w[q].y; }
-    __syncthreads();
-    piv_put(B22, kNb, z);
-    piv_put(B21, kNb, w);
+  piv_mm(B21, kNb, half ? B11 : B12, kNb, s, 0, kPivH, u);  // A21 B12 | A21 P1
+  __syncthreads();
+  if (!half) {
+    piv_neg(u);
+    piv_acc(B22, kNb, s, 1.f, u);
+    piv_put(B22, kNb, s, u);  // B22 <- A22 - A21 B12
+  } else {
+    piv_neg(u);
+    piv_put(B21, kNb, s, u);  // B21 <- -A21 P1
   }
   __syncthreads();
   piv_gj64(M, kPivH, sh);  // B22 <- X22
   __syncthreads();
-  piv_gemm64(B12, kNb, B22, kNb, u);  // B12 X22
-#pragma unroll
-  for (int q = 0; q < 4; ++q) { u[q].x = -u[q].x; u[q].y = -u[q].y; }
-  piv_put(T, kPivH, u);  // V
+  piv_mm(B12, kNb, B22, kNb, s, 32 * half, 32, u);  // B12 X22
+  if (half) piv_put(T, kPivH, s, u);
   __syncthreads();
-  piv_gemm64(B22, kNb, B21, kNb, u);  // X22 B21
-  piv_gemm64(T, kPivH, B21, kNb, w);  // V B21
-  {
-    float2 p1[4], v[4];
-    piv_get(B11, kNb, p1);
-    piv_get(T, kPivH, v);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { w[q].x += p1[q].x; w[q].y += p1[q].y; }
-    __syncthreads();
-    piv_put(B21, kNb, u);
-    piv_put(B11, kNb, w);
-    piv_put(B12, kNb, v);
+  if (!half) {
+    piv_acc(T, kPivH, s, 1.f, u);
+    piv_neg(u);
+    piv_put(T, kPivH, s, u);  // V = -B12 X22
+  }
+  __syncthreads();
+  piv_mm(half ? T : B22, half ? kPivH : kNb, B21, kNb, s, 0, kPivH, u);  // X22 B21 | V B21
+  __syncthreads();
+  if (!half) {
+    piv_put(B21, kNb, s, u);  // B21 <- X22 B21
+    float2 v[4][2] = {};
+    piv_acc(T, kPivH, s, 1.f, v);
+    piv_put(B12, kNb, s, v);  // B12 <- V
+  } else {
+    piv_acc(B11, kNb, s, 1.f, u);
+    piv_put(B11, kNb, s, u);  // B11 <- P1 + V B21
   }
   __syncthreads();
   if (sh.bad && t == 0 && status) atomicCAS(status, 0, DS_SINGULAR);
