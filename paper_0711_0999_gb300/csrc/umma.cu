@@ -715,12 +715,16 @@ struct EpiRPack {
 constexpr int kPivH = kNb / 2;
 constexpr size_t kPivSmem = (size_t)(kNb * kNb + kPivH * kPivH) * sizeof(float2);  // 160 KB
 
-struct PivShared {
+struct alignas(16) PivShared {
   float2 rowb[2][kPivH], colb[2][kPivH], pivb[2];
   int bad;
 };
 
-// unblocked in-place Gauss-Jordan of the 64 x 64 block of M (row stride kNb) at (o, o)
+// unblocked in-place Gauss-Jordan of the 64 x 64 block of M (row stride kNb) at (o, o).
+// Pivot k: the pivot row is broadcast with its pivot entry replaced by 1, so
+// every row r != k takes a[r][c] <- [c != k] a[r][c] - g_r rowb[c] with
+// g_r = a[r][k] / p (column k becomes -g_r); the warp holding row k (2 rows
+// per warp) scales that row by 1 / p.
 __device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
   const int t = threadIdx.x;
   const int rr = 2 * (t >> 5), cc = 2 * (t & 31);
@@ -738,12 +742,14 @@ __device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
         if (rr + i == k) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            sh.rowb[buf][cc + j] = a[i][j];
+            float2 v = a[i][j];
             if (cc + j == k) {
               float2 pinv;
               if (!cinv_guard<float>(a[i][j], pinv, 1e-6f)) sh.bad = 1;
               sh.pivb[buf] = pinv;
+              v = make_float2(1.f, 0.f);
             }
+            sh.rowb[buf][cc + j] = v;
           }
         }
     }
@@ -756,23 +762,21 @@ __device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
     }
     __syncthreads();
     const float2 pinv = sh.pivb[buf];
-    float2 rk[2], g[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) rk[j] = sh.rowb[buf][cc + j];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) g[i] = cmul(sh.colb[buf][rr + i], pinv);
+    const float4 r4 = *reinterpret_cast<const float4*>(&sh.rowb[buf][cc]);
+    const float4 c4 = *reinterpret_cast<const float4*>(&sh.colb[buf][rr]);
+    const float2 rk[2] = {make_float2(r4.x, r4.y), make_float2(r4.z, r4.w)};
+    const float2 g[2] = {cmul(make_float2(c4.x, c4.y), pinv), cmul(make_float2(c4.z, c4.w), pinv)};
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const int r = rr + i, c = cc + j;
-        if (r == k) {
-          a[i][j] = (c == k) ? pinv : cmul(rk[j], pinv);
-        } else if (c == k) {
-          a[i][j] = make_float2(-g[i].x, -g[i].y);
+        if (row_k && rr + i == k) {
+          a[i][j] = (cc + j == k) ? pinv : cmul(a[i][j], pinv);
         } else {
-          a[i][j].x -= g[i].x * rk[j].x - g[i].y * rk[j].y;
-          a[i][j].y -= g[i].x * rk[j].y + g[i].y * rk[j].x;
+          float2 v = (cc + j == k) ? make_float2(0.f, 0.f) : a[i][j];
+          v.x -= g[i].x * rk[j].x - g[i].y * rk[j].y;
+          v.y -= g[i].x * rk[j].y + g[i].y * rk[j].x;
+          a[i][j] = v;
         }
       }
   }
