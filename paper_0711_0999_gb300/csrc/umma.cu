@@ -1812,10 +1812,10 @@ __global__ void __launch_bounds__(256) reduce_refined_kernel(ContourDev c, Model
   }
   __syncthreads();
   const size_t total = (size_t)c.n * c.n, mat = (size_t)np * np;
-  const int row_blocks = c.n;
-  for (int i = blockIdx.x; i < row_blocks; i += gridDim.x) {
-    for (int j = threadIdx.x; j < c.n; j += blockDim.x) {
-      const size_t e = (size_t)i * c.n + j;
+  // entries e = i n + j dealt evenly to all threads (consecutive threads, consecutive j)
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    {
+      const int i = (int)(e / c.n), j = (int)(e - (size_t)i * c.n);
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
       const int j0 = j, j1 = (j == 0 ? c.n - 1 : j - 1);
       // eight matrices' loads in flight at a time; the sum still runs over b in order
@@ -1855,16 +1855,16 @@ __global__ void __launch_bounds__(256) reduce_refined_kernel(ContourDev c, Model
       gloc[e] = acc;
     }
   }
-  (void)total;
 }
 
-__global__ void reduce_refined_current_kernel(ContourDev c, ModelDev mo, const double* __restrict__ eps_d,
-                                              const double* __restrict__ ebar_d, const double* __restrict__ wq_d,
-                                              int q0, int nb, const float2* __restrict__ X,
-                                              const float2* __restrict__ dX, const int* __restrict__ flags, int np,
-                                              bool first, double2* __restrict__ jacc) {
-  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
-  if (mm >= c.nt) return;
+// One warp per time t_m: lane l takes the points b = l, l + 32, ... of the
+// batch, and the lanes' partial sums are added in a fixed shuffle tree.
+__global__ void __launch_bounds__(256) reduce_refined_current_kernel(
+    ContourDev c, ModelDev mo, const double* __restrict__ eps_d, const double* __restrict__ ebar_d,
+    const double* __restrict__ wq_d, int q0, int nb, const float2* __restrict__ X, const float2* __restrict__ dX,
+    const int* __restrict__ flags, int np, bool first, double2* __restrict__ jacc) {
+  const int mm = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (mm >= c.nt) return;  // whole warps
   const double t = t_re(c, mm);
   const int jcol = 2 * c.nt - mm;
   const size_t mat = (size_t)np * np;
@@ -1872,32 +1872,28 @@ __global__ void reduce_refined_current_kernel(ContourDev c, ModelDev mo, const d
   // trigonometric factors are the same for every point
   double sn = 0.0, cs = 1.0;
   if (t > 0.0) sincos(mo.E * t, &sn, &cs);
-  double2 acc = first ? make_double2(0.0, 0.0) : jacc[mm];
-  constexpr int U = 8;  // loads of eight points in flight; the sum runs over b in order
-  for (int b0 = 0; b0 < nb; b0 += U) {
-    double2 vs[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int b = b0 + u;
-      vs[u] = make_double2(0.0, 0.0);
-      if (b < nb) {
-        const int q = q0 + b;
-        const size_t off = b * mat + (size_t)mm * np + unshift_col(jcol, c.n, shifted_point(mo, eps_d[q]));
-        vs[u] = to_d(X[off]);
-        if (flags[q]) vs[u] = cadd(vs[u], to_d(dX[off]));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int b = b0 + u;
-      if (b >= nb) break;
-      const int q = q0 + b;
-      const double w = wq_d[q] * (ebar_d[q] * cs + eps_d[q] * sn);
-      acc.x = fma(w, vs[u].x, acc.x);
-      acc.y = fma(w, vs[u].y, acc.y);
-    }
+  double2 part = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int b = lane; b < nb; b += 32) {
+    const int q = q0 + b;
+    const size_t off = b * mat + (size_t)mm * np + unshift_col(jcol, c.n, shifted_point(mo, eps_d[q]));
+    double2 v = to_d(X[off]);
+    if (flags[q]) v = cadd(v, to_d(dX[off]));
+    const double w = wq_d[q] * (ebar_d[q] * cs + eps_d[q] * sn);
+    part.x = fma(w, v.x, part.x);
+    part.y = fma(w, v.y, part.y);
   }
-  jacc[mm] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+    part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+  }
+  if (lane == 0) {
+    double2 acc = first ? make_double2(0.0, 0.0) : jacc[mm];
+    acc.x += part.x;
+    acc.y += part.y;
+    jacc[mm] = acc;
+  }
 }
 
 // Refinement buffers, each an array over the batch.
@@ -2049,15 +2045,16 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
     NED_LAUNCH_CHECK("umma_gemm_flag_kernel");
   }
   {
-    const size_t total = (size_t)c.n * c.n;
-    int bx = (int)((total + 255) / 256);
-    if (bx > 152 * 8) bx = 152 * 8;
+    // as many rounds of 152 x 8 blocks as the entries need, then just enough
+    // blocks for that many rounds, so every thread takes the same count
+    const size_t total = (size_t)c.n * c.n, wave = (size_t)152 * 8 * 256;
+    const size_t rounds = total > wave ? (total + wave - 1) / wave : 1;
+    const int bx = total ? (int)((total + rounds * 256 - 1) / (rounds * 256)) : 1;
     if (nb > kRedMaxBatch) return set_error(NEDMFT_EINVAL, "reduce: batch %d > %d", nb, kRedMaxBatch);
-    reduce_refined_kernel<<<c.n < 152 * 8 ? c.n : 152 * 8, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dx, sh.flags, np,
-                                                                       first, gloc);
+    reduce_refined_kernel<<<bx, 256, 0, st>>>(c, m, eps, wq, q0, nb, X, dx, sh.flags, np, first, gloc);
     NED_LAUNCH_CHECK("reduce_refined_kernel");
     if (jacc) {
-      reduce_refined_current_kernel<<<ceil_div(c.nt, 128), 128, 0, st>>>(c, m, eps, ebar, wq, q0, nb, X, dx,
+      reduce_refined_current_kernel<<<ceil_div(c.nt, 8), 256, 0, st>>>(c, m, eps, ebar, wq, q0, nb, X, dx,
                                                                          sh.flags, np, first, jacc);
       NED_LAUNCH_CHECK("reduce_refined_current_kernel");
     }
