@@ -1527,6 +1527,8 @@ struct OzParams {
 constexpr int kOzHalfA = kTileBytes / 2, kOzHalfB = kTileBytes / 4;
 constexpr int kOzStageBytes = kOzS * (kOzHalfA + kOzHalfB);  // 48 KB
 constexpr int kOzStages = 4;
+constexpr int kOzEpiW = 8;                     // epilogue warps: two per TMEM lane quarter
+constexpr int kOzEpiCols = kOzBn * 4 / kOzEpiW;  // accumulator columns per epilogue thread
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 
 // Persistent, in clusters of two CTAs: the units (refined matrix, m tile, pair
@@ -1538,7 +1540,7 @@ constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 // Chunks of kOzChunkKt K tiles alternate between two TMEM buffers of kOzS
 // accumulators of kOzBn columns across units, so the epilogue drains (and
 // finishes a unit) while the next chunk is multiplied.
-__global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_constant__ OzParams p) {
+__global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
@@ -1565,7 +1567,7 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], 128);
+      mbar_init(&acc_empty[s], 32 * kOzEpiW);
     }
     *abort_flag = 0;
     fence_barrier_init();
@@ -1657,8 +1659,11 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
       }
     }
   } else {
+    // kOzEpiW epilogue warps: warp w owns TMEM lanes 32 (w % 4) .. +31 (rows of
+    // the tile) and columns kOzEpiCols (w - 2) / 4 .. + kOzEpiCols - 1 of each order
     const int q = warp & 3;
     const int row = q * 32 + lane;
+    const int part = (warp - 2) >> 2;
     bool ok = true;
     int cg = 0;
     for (int u = cl; u < units && ok; u += G) {
@@ -1670,11 +1675,11 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
       const int r = (i < n && sh) ? (i == 0 ? n - 1 : i - 1) : i;  // row of R' fed by row i
       const int ei = p.a_exp[i];
       const int* xe = p.b_exp + (size_t)bidx * np;
-      const int j0 = nt * (kOzBn / 2);
+      const int j0 = nt * (kOzBn / 2) + part * (kOzEpiCols / 2);  // this thread's first complex column
       // The sums start from T - (B - S_sp) X' at (i, j) (double-float, in the
       // accumulator's units 2^(e_i + e_j)), so the reads of X' rows (16-byte
       // vectors) overlap the products of the unit's first chunk.
-      float hs[kOzBn], ls[kOzBn];
+      float hs[kOzEpiCols], ls[kOzEpiCols];
       {
         const float2* x = p.X + (size_t)bidx * np * np;
         const float4* cf = p.coef + (size_t)bidx * np * 3;
@@ -1685,7 +1690,7 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
         const int io = i == 0 ? n - 1 : i - 1;
         const float4* xo = i < n ? reinterpret_cast<const float4*>(x + (size_t)io * np + j0) : nullptr;
 #pragma unroll
-        for (int v = 0; v < kOzBn / 4; ++v) {  // two complex columns per vector
+        for (int v = 0; v < kOzEpiCols / 4; ++v) {  // two complex columns per vector
           const float4 zd = xd[v];
           const float4 zo = xo ? xo[v] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -1718,9 +1723,9 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
         for (int d = 0; d < kOzS; ++d) {
           const float sc = ldexpf(1.0f, -kOzBits * (d + 2));
 #pragma unroll
-          for (int pc = 0; pc < kOzBn / 32; ++pc) {
+          for (int pc = 0; pc < kOzEpiCols / 32; ++pc) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + d * kOzBn + pc * 32, v);
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + d * kOzBn + part * kOzEpiCols + pc * 32, v);
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               float s, er;
@@ -1737,7 +1742,7 @@ __global__ void __launch_bounds__(192, 1) oz_residual_kernel(const __grid_consta
       __nv_bfloat16* ri = p.rimg + bidx * p.r_batch;
       const int kt = 2 * np / kTileK;
 #pragma unroll
-      for (int uu = 0; uu < kOzBn / 2; ++uu) {
+      for (int uu = 0; uu < kOzEpiCols / 2; ++uu) {
         const int j = j0 + uu;
         const int sc = ei + xe[j];
         const float tr_h = ldexpf(hs[2 * uu], sc), tr_l = ldexpf(ls[2 * uu], sc);
@@ -2016,7 +2021,7 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(192);
+    cfg.blockDim = dim3(64 + 32 * kOzEpiW);
     cfg.dynamicSmemBytes = kOzSmem;
     cfg.stream = st;
     cfg.attrs = attr;
