@@ -716,69 +716,100 @@ constexpr int kPivH = kNb / 2;
 constexpr size_t kPivSmem = (size_t)(kNb * kNb + kPivH * kPivH) * sizeof(float2);  // 160 KB
 
 struct alignas(16) PivShared {
-  float2 rowb[2][kPivH], colb[2][kPivH], pivb[2];
+  float4 rowb[2][2][kPivH / 2];  // [buffer][pivot row][column pair]
+  float4 colb[2][kPivH];         // [buffer][row]: the row's two entries in the pivot columns
+  float4 pivb[2][2];             // [buffer][row of P^-1]
   int bad;
 };
 
-// unblocked in-place Gauss-Jordan of the 64 x 64 block of M (row stride kNb) at (o, o).
-// Pivot k: the pivot row is broadcast with its pivot entry replaced by 1, so
-// every row r != k takes a[r][c] <- [c != k] a[r][c] - g_r rowb[c] with
-// g_r = a[r][k] / p (column k becomes -g_r); the warp holding row k (2 rows
-// per warp) scales that row by 1 / p.
+__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// unblocked in-place Gauss-Jordan of the 64 x 64 block of M (row stride kNb) at (o, o),
+// two pivots per barrier: thread (warp w, lane l) holds rows 2w, 2w+1 x columns 2l, 2l+1,
+// so step s eliminates with the 2 x 2 pivot block P held by thread (s, s) (P^-1 by
+// two scalar pivots: p11 and the Schur complement p22 - p21 p11^-1 p12).  Warp s
+// broadcasts its rows A_K with the pivot columns replaced by the identity and turns
+// them into P^-1 A_K (P^-1 in the pivot columns); every other row r takes
+// a[r][c] <- [c not a pivot column] a[r][c] - g_r rowb[:, c] with g_r = a[r][K] P^-1
+// (so its pivot columns become -g_r).
 __device__ __forceinline__ void piv_gj64(float2* M, int o, PivShared& sh) {
-  const int t = threadIdx.x;
-  const int rr = 2 * (t >> 5), cc = 2 * (t & 31);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int rr = 2 * w, cc = 2 * lane;
   float2 a[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) a[i][j] = M[(o + rr + i) * kNb + o + cc + j];
-  for (int k = 0; k < kPivH; ++k) {
-    const int buf = k & 1;
-    const bool row_k = (k >> 1) == (rr >> 1), col_k = (k >> 1) == (cc >> 1);
-    if (row_k) {
+  for (int s = 0; s < kPivH / 2; ++s) {
+    const int buf = s & 1;
+    if (lane == s)  // the rows' entries in the pivot columns, before the step
 #pragma unroll
       for (int i = 0; i < 2; ++i)
-        if (rr + i == k) {
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            float2 v = a[i][j];
-            if (cc + j == k) {
-              float2 pinv;
-              if (!cinv_guard<float>(a[i][j], pinv, 1e-6f)) sh.bad = 1;
-              sh.pivb[buf] = pinv;
-              v = make_float2(1.f, 0.f);
-            }
-            sh.rowb[buf][cc + j] = v;
-          }
-        }
-    }
-    if (col_k) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (cc + j == k)
-#pragma unroll
-          for (int i = 0; i < 2; ++i) sh.colb[buf][rr + i] = a[i][j];
-    }
-    __syncthreads();
-    const float2 pinv = sh.pivb[buf];
-    const float4 r4 = *reinterpret_cast<const float4*>(&sh.rowb[buf][cc]);
-    const float4 c4 = *reinterpret_cast<const float4*>(&sh.colb[buf][rr]);
-    const float2 rk[2] = {make_float2(r4.x, r4.y), make_float2(r4.z, r4.w)};
-    const float2 g[2] = {cmul(make_float2(c4.x, c4.y), pinv), cmul(make_float2(c4.z, c4.w), pinv)};
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
+        sh.colb[buf][rr + i] = make_float4(a[i][0].x, a[i][0].y, a[i][1].x, a[i][1].y);
+    if (w == s) {  // warp-uniform: the pivot rows
+      float2 q00 = make_float2(0.f, 0.f), q01 = q00, q10 = q00, q11 = q00;
+      if (lane == s) {
+        float2 i1, is;
+        const bool ok1 = cinv_guard<float>(a[0][0], i1, 1e-6f);
+        const float2 t12 = cmul(i1, a[0][1]);  // p11^-1 p12
+        const float2 t21 = cmul(a[1][0], i1);  // p21 p11^-1
+        const bool ok2 = cinv_guard<float>(csub(a[1][1], cmul(a[1][0], t12)), is, 1e-6f);
+        if (!ok1 || !ok2) sh.bad = 1;
+        const float2 u = cmul(t12, is);
+        q00 = cadd(i1, cmul(u, t21));
+        q01 = make_float2(-u.x, -u.y);
+        const float2 v = cmul(is, t21);
+        q10 = make_float2(-v.x, -v.y);
+        q11 = is;
+        sh.pivb[buf][0] = make_float4(q00.x, q00.y, q01.x, q01.y);
+        sh.pivb[buf][1] = make_float4(q10.x, q10.y, q11.x, q11.y);
+      }
+      q00 = shfl_c(q00, s);
+      q01 = shfl_c(q01, s);
+      q10 = shfl_c(q10, s);
+      q11 = shfl_c(q11, s);
+      float2 r0[2], r1[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        if (row_k && rr + i == k) {
-          a[i][j] = (cc + j == k) ? pinv : cmul(a[i][j], pinv);
-        } else {
-          float2 v = (cc + j == k) ? make_float2(0.f, 0.f) : a[i][j];
-          v.x -= g[i].x * rk[j].x - g[i].y * rk[j].y;
-          v.y -= g[i].x * rk[j].y + g[i].y * rk[j].x;
+        r0[j] = cadd(cmul(q00, a[0][j]), cmul(q01, a[1][j]));
+        r1[j] = cadd(cmul(q10, a[0][j]), cmul(q11, a[1][j]));
+      }
+      if (lane == s) {
+        sh.rowb[buf][0][lane] = make_float4(1.f, 0.f, 0.f, 0.f);
+        sh.rowb[buf][1][lane] = make_float4(0.f, 0.f, 1.f, 0.f);
+        a[0][0] = q00; a[0][1] = q01;
+        a[1][0] = q10; a[1][1] = q11;
+      } else {
+        sh.rowb[buf][0][lane] = make_float4(a[0][0].x, a[0][0].y, a[0][1].x, a[0][1].y);
+        sh.rowb[buf][1][lane] = make_float4(a[1][0].x, a[1][0].y, a[1][1].x, a[1][1].y);
+        a[0][0] = r0[0]; a[0][1] = r0[1];
+        a[1][0] = r1[0]; a[1][1] = r1[1];
+      }
+    }
+    __syncthreads();
+    if (w != s) {
+      const float4 p0 = sh.pivb[buf][0], p1 = sh.pivb[buf][1];
+      const float4 b0 = sh.rowb[buf][0][lane], b1 = sh.rowb[buf][1][lane];
+      const float2 rk0[2] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w)};
+      const float2 rk1[2] = {make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float4 c4 = sh.colb[buf][rr + i];
+        const float2 x0 = make_float2(c4.x, c4.y), x1 = make_float2(c4.z, c4.w);
+        // g = (x0, x1) P^-1
+        const float2 g0 = cadd(cmul(x0, make_float2(p0.x, p0.y)), cmul(x1, make_float2(p1.x, p1.y)));
+        const float2 g1 = cadd(cmul(x0, make_float2(p0.z, p0.w)), cmul(x1, make_float2(p1.z, p1.w)));
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float2 v = lane == s ? make_float2(0.f, 0.f) : a[i][j];
+          v.x -= g0.x * rk0[j].x - g0.y * rk0[j].y + g1.x * rk1[j].x - g1.y * rk1[j].y;
+          v.y -= g0.x * rk0[j].y + g0.y * rk0[j].x + g1.x * rk1[j].y + g1.y * rk1[j].x;
           a[i][j] = v;
         }
       }
+    }
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i)
