@@ -68,37 +68,70 @@ def _oracle_worker(task):
     return acc
 
 
-def oracle_sample(n_points: int | None = None):
-    """Time the oracle on a bounded sample of the workload's points on all host cores.
+class OracleTimer:
+    """The oracle, as it stands, on bounded samples of the workload's points, on
+    all host cores: one spawned process pool (one BLAS thread per process) that
+    lives across warm-up and timed steps."""
 
-    Returns (lattice steps/s extrapolated from the sample, cores, sample text)."""
-    import multiprocessing as mp
+    def __init__(self):
+        import multiprocessing as mp
 
-    from oracle import nedmft_oracle as O
-    from paper_0711_0999_gb300.synth import workload_sigma
+        from oracle import nedmft_oracle as O
+        from paper_0711_0999_gb300.synth import workload_sigma
 
-    W = WORKLOAD
-    cores = os.cpu_count() or 1
-    npts = n_points or 5 * cores  # about 12 s of CPU work on 16 cores
-    c = O.contour_grid(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"])
-    sigma = workload_sigma(c.t, c.w, W["U"])
-    eps, ebar, _ = O.quadrature_points(W["n_quad"])
-    nq = len(eps)
-    idx = np.linspace(0, nq - 1, npts).round().astype(int)
-    per = [[(float(eps[i]), float(ebar[i]))] for i in idx]
-    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[k] = "1"
-    ctx = mp.get_context("spawn")
-    tasks = [(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"], W["U"], W["E"], sigma, p) for p in per]
-    with ctx.Pool(processes=min(cores, npts)) as pool:
-        pool.map(_oracle_worker, tasks[: min(cores, npts)])  # start-up and import outside the timing
+        W = WORKLOAD
+        self.cores = os.cpu_count() or 1
+        self.c = O.contour_grid(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"])
+        self.sigma = workload_sigma(self.c.t, self.c.w, W["U"])
+        self.eps, self.ebar, _ = O.quadrature_points(W["n_quad"])
+        self.nq = len(self.eps)
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.pool = mp.get_context("spawn").Pool(processes=self.cores)
+
+    def _tasks(self, npts):
+        W = WORKLOAD
+        idx = np.linspace(0, self.nq - 1, npts).round().astype(int)
+        return [(W["t_min"], W["t_max"], W["dt"], W["beta"], W["dtau"], W["U"], W["E"], self.sigma,
+                 [(float(self.eps[i]), float(self.ebar[i]))]) for i in idx]
+
+    def warm(self):
+        """One point per process, untimed (process start-up, imports, first solve)."""
+        self.pool.map(_oracle_worker, self._tasks(self.cores))
+
+    def time(self, npts: int):
+        """Lattice steps/s extrapolated from `npts` evenly spread points, the
+        processes used, and a description of the sample."""
+        tasks = self._tasks(npts)
         t0 = time.perf_counter()
-        pool.map(_oracle_worker, tasks)
+        self.pool.map(_oracle_worker, tasks)
         dt = time.perf_counter() - t0
-    steps_per_s = (npts / dt) / nq
-    sample = (f"{npts} of {nq} points of the N_c={c.n_c} workload (G0 build + solve(I - G0 S, G0) each), "
-              f"{min(cores, npts)} processes x 1 BLAS thread, {dt:.1f} s, scaled by {nq}/{npts}")
-    return steps_per_s, min(cores, npts), sample
+        used = min(self.cores, npts)
+        sample = (f"{npts} of {self.nq} points of the N_c={self.c.n_c} workload (G0 build + solve(I - G0 S, G0) "
+                  f"each), {used} processes x 1 BLAS thread, {dt:.1f} s, scaled by {self.nq}/{npts}")
+        return (npts / dt) / self.nq, used, sample
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_sample(n_points: int | None = None):
+    """One timed sample (default 5 points per host core, about 12 s of CPU work on
+    16 cores) after one warm-up round: (lattice steps/s, cores, sample text)."""
+    t = OracleTimer()
+    try:
+        t.warm()
+        return t.time(n_points or 5 * t.cores)
+    finally:
+        t.close()
+
+
+def reference_points_per_step(cores: int, steps: int) -> int:
+    """Points per timed step of the reference arm: 5 per core for up to 5 steps,
+    then fewer (never under one per core), so that K steps together stay at about
+    25 points per core (about a minute of CPU work) whatever K is."""
+    return max(cores, (25 * cores) // max(steps, 5))
 
 
 # ------------------------------------------------------------------ clocks
@@ -133,24 +166,32 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[3:7]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        with open(self.path) as fh:
+            return parse_clocks(fh)
+
+
+def parse_clocks(lines):
+    """Summary of nvidia-smi samples in ClockSampler.FIELDS order: the median SM
+    clock, the maximum SM clock, the sample count and every throttle reason seen
+    active in any sample; None without a valid sample."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 7:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax.append(float(parts[1]))
+        except ValueError:
+            continue
+        for name, val in zip(names, parts[3:7]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+            "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------------ peaks
@@ -207,9 +248,16 @@ def run_reference(args, rank, world):
         return
     steps_per_s = []
     cores = sample = None
-    for _ in range(args.steps):
-        v, cores, sample = oracle_sample(args.cpu_points or None)
-        steps_per_s.append(v)
+    t = OracleTimer()
+    try:
+        for _ in range(max(args.warmup, 1)):
+            t.warm()
+        npts = args.cpu_points or reference_points_per_step(t.cores, args.steps)
+        for _ in range(args.steps):
+            v, cores, sample = t.time(npts)
+            steps_per_s.append(v)
+    finally:
+        t.close()
     v = statistics.median(steps_per_s)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iterations/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
