@@ -1092,7 +1092,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// the driver's tensor-map encoder, looked up once (no link against the driver library)
+// the CUDA driver's tensor-map encoder, looked up once (no link against libcuda)
 EncodeTiledFn encode_tiled_fn() {
   static const EncodeTiledFn fn = [] {
     void* f = nullptr;
@@ -1110,7 +1110,7 @@ EncodeTiledFn encode_tiled_fn() {
 int encode_f32_rows(CUtensorMap* map, float* base, uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows,
                     CUtensorMapSwizzle swizzle) {
   const EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {cols * sizeof(float)};
   const cuuint32_t box[2] = {box_cols, box_rows};
@@ -1130,7 +1130,7 @@ namespace {
 // `base`, moved in half tiles: box (64 elements, 4 core columns, 16 row groups, 1).
 int encode_tile_map(CUtensorMap* map, void* base, uint64_t tiles) {
   const EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   const cuuint64_t dims[4] = {64, 8, 16, tiles};
   const cuuint64_t strides[3] = {128, 1024, 16384};
   const cuuint32_t box[4] = {64, 4, 16, 1};
@@ -1989,7 +1989,7 @@ namespace {
 // half tiles of `rgroups` 8-row groups: box (64 elements, 4 core columns, rgroups, 1).
 int encode_oz_map(CUtensorMap* map, void* base, uint64_t tiles, uint32_t rgroups) {
   const EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (!fn) return set_error(NEDMFT_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   const cuuint64_t dims[4] = {64, 8, 16, tiles};
   const cuuint64_t strides[3] = {128, 1024, 16384};
   const cuuint32_t box[4] = {64, 4, rgroups, 1};
