@@ -67,8 +67,12 @@ typedef enum {
   /* FP64 Gauss-Jordan inversion of each B_q - S (DFMA). */
   NEDMFT_FP64 = 0,
   /* bf16x3 (hi*hi + hi*lo + lo*hi) tcgen05 tensor-core Gauss-Jordan with
-   * FP32 accumulation in TMEM, then one refinement step whose residual
-   * I - A X is formed with the bidiagonal part in FP64; the sum over q is
+   * FP32 accumulation in TMEM; then, for every point outside the
+   * smallest-weight tail (total weight <= 1e-3 of the sum), one refinement
+   * step X + X R with R = I - A X, whose entries of S on the pattern of B_q
+   * are applied in double-float and whose dense rest S_d X runs as an exact
+   * Ozaki split on the bf16 tensor cores (4 slices of 7 bits, exact chunk
+   * sums combined in double-float); the sum over q is double-float, then
    * FP64. */
   NEDMFT_MIXED_BF16 = 1,
   /* the same algorithm with FP32 CUDA-core products (no tensor cores). */
@@ -306,7 +310,9 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  *   A0 = inv(G_loc) + S,  A1 = A0 + i [M(mu - U) - M(mu)],
  *   G_imp = (1 - w1) inv(A0) + w1 inv(A1),
  *   sigma_new = W^-1 (A0 - inv(G_imp)) W^-1.
- * Inversions: Gauss-Jordan with partial pivoting.  gimp_d may be NULL.
+ * Inversions: blocked Gauss-Jordan (32 columns per step) whose pivot rows a
+ * tournament of partial-pivoting rounds on 256-row chunks chooses.  gimp_d
+ * may be NULL.
  * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered. */
 int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
                            const nedmft_c128* gloc_d,
