@@ -73,10 +73,10 @@ typedef enum {
    * are applied in double-float and whose dense rest S_d X runs as an exact
    * Ozaki split on the bf16 tensor cores (4 slices of 7 bits, exact chunk
    * sums combined in double-float); the sum over q is double-float, then
-   * FP64. */
-  NEDMFT_MIXED_BF16 = 1,
-  /* the same algorithm with FP32 CUDA-core products (no tensor cores). */
-  NEDMFT_MIXED_FP32 = 2
+   * FP64.  (Three bf16 products per FP32-accurate product: no TF32 variant,
+   * since one TF32 product keeps only 11 mantissa bits and three of them run
+   * slower than three bf16 products.) */
+  NEDMFT_MIXED_BF16 = 1
 } nedmft_precision;
 
 /* ---------------------------------------------------------------- status */
@@ -98,8 +98,28 @@ const char* nedmft_version(void);
 
 /* Synchronise `stream`, read and clear the device status word (set by the
  * kernels on a bad pivot or an expired wait).  Returns NEDMFT_OK,
- * NEDMFT_ESINGULAR or NEDMFT_ETIMEOUT. */
+ * NEDMFT_ESINGULAR or NEDMFT_ETIMEOUT.  A non-finite input (a NaN or an
+ * infinity in Sigma or G_loc) reaches a pivot of the Gauss-Jordan
+ * elimination, where it counts as a pivot below the threshold:
+ * NEDMFT_ESINGULAR. */
 int nedmft_check_status(void* stream);
+
+/* Failure detection of the tensor-core kernels.  Every wait of those kernels
+ * for work (a filled or a free pipeline stage, an accumulator) is bounded: it
+ * gives up after the device's wait limit, the kernel stops issuing work,
+ * waits (for at most 2 s) for the copies and products it already issued,
+ * releases its tensor memory, records NEDMFT_ETIMEOUT in the status word and
+ * returns; the context stays usable and the outputs of that call are
+ * undefined.
+ * nedmft_set_wait_limit sets the limit on the current device (default 2 s;
+ * seconds in [0, 60]; 0 makes every wait that is not satisfied at once give
+ * up, which only a test of this path wants).  Synchronises `stream` and
+ * applies to kernels launched after it returns.
+ * nedmft_wait_selftest launches one kernel that waits, bounded by that
+ * limit, on a barrier that nothing arrives at: nedmft_check_status then
+ * returns NEDMFT_ETIMEOUT.  Stream-ordered. */
+int nedmft_set_wait_limit(double seconds, void* stream);
+int nedmft_wait_selftest(void* stream);
 
 /* ---------------------------------------------------------------- instrumentation */
 
@@ -233,7 +253,8 @@ int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
                    nedmft_precision prec, double* j_d, double* j_imag_d,
                    void* ws_d, size_t ws_bytes, void* stream);
 
-/* Batch autotuner (scope table: the tile/batch choice per N_c).  Times one
+/* Batch autotuner (a choice the paper leaves to the machine: how many
+ * quadrature points, its independent solves of Sec. II, run at once).  Times one
  * lattice step (after an untimed one) with each candidate number of points
  * per batch that fits the workspace, and records the fastest for this
  * (n_c, nq, prec); later calls of nedmft_lattice_workspace_size(..., batch = 0),
@@ -307,12 +328,16 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  * dynamical_mean_field, g_imp_solve; the M matrix of the discretised
  * (i d/dt + mu) delta_c; the operator inverse of Eq.
  * matrix_inverse_discrete):
- *   A0 = inv(G_loc) + S,  A1 = A0 + i [M(mu - U) - M(mu)],
+ *   A0 = inv(G_loc) + S,  A1 = A0 + D with D = i [M(mu - U) - M(mu)],
  *   G_imp = (1 - w1) inv(A0) + w1 inv(A1),
  *   sigma_new = W^-1 (A0 - inv(G_imp)) W^-1.
- * Inversions: blocked Gauss-Jordan (32 columns per step) whose pivot rows a
- * tournament of partial-pivoting rounds on 256-row chunks chooses.  gimp_d
- * may be NULL.
+ * Evaluated with two inversions instead of four: with A_h = A0 + (1 - w1) D,
+ * G_imp = inv(A0) A_h inv(A1), so A0 - inv(G_imp) = -w1 D + w1 (1 - w1)
+ * D inv(A_h) D, and D (one entry per row, -U W_j at (j, j-1), +U W_0 at
+ * (0, N-1)) makes the last product a gather.  Inversions: blocked
+ * Gauss-Jordan (32 columns per step) whose pivot rows a tournament of
+ * partial-pivoting rounds on 256-row chunks chooses.  gimp_d may be NULL;
+ * if given, G_imp = inv(A0 - W sigma_new W) costs a third inversion.
  * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered. */
 int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
                            const nedmft_c128* gloc_d,
@@ -394,8 +419,8 @@ int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
                       nedmft_c128* gloc_d, double* j_d, int32_t* iters,
                       double* err, void* ws_d, size_t ws_bytes, void* stream);
 
-/* Several DMFT runs at once (scope table: ragged batching of many (U, E, dt)
- * runs): run r has its own contour (n_c may differ between runs) and model,
+/* Several DMFT runs at once (the paper's workflow: runs at several (U, E)
+ * and several dt for the Lagrange extrapolation of Sec. II): run r has its own contour (n_c may differ between runs) and model,
  * all share n_quad and prec.  Every sweep takes one iteration of each run that
  * is still active -- impurity step, lattice step, convergence norm, all on one
  * stream without a host sync in between -- and synchronises once; a run leaves

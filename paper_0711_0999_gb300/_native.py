@@ -28,8 +28,7 @@ NEDMFT_ENOTCONV = 1
 
 FP64 = 0
 MIXED_BF16 = 1
-MIXED_FP32 = 2
-PRECISIONS = {"fp64": FP64, "mixed_bf16": MIXED_BF16, "mixed_fp32": MIXED_FP32}
+PRECISIONS = {"fp64": FP64, "mixed_bf16": MIXED_BF16}
 
 
 class Contour(ctypes.Structure):
@@ -58,6 +57,8 @@ SIGNATURES = {
     "nedmft_last_error": (ctypes.c_char_p, []),
     "nedmft_version": (ctypes.c_char_p, []),
     "nedmft_check_status": (ctypes.c_int, [c_void_p]),
+    "nedmft_set_wait_limit": (ctypes.c_int, [c_double, c_void_p]),
+    "nedmft_wait_selftest": (ctypes.c_int, [c_void_p]),
     "nedmft_instrument": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "nedmft_instrument_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), PD, PD,
                                                PD]),

@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _native as N
-from ._native import FP64, MIXED_BF16, MIXED_FP32, NedmftError, PRECISIONS  # noqa: F401
+from ._native import FP64, MIXED_BF16, NedmftError, PRECISIONS  # noqa: F401
 
 
 def _prec(p) -> int:
@@ -45,6 +45,16 @@ def version() -> str:
 
 def check_status(stream=None) -> None:
     N.check(N.lib().nedmft_check_status(ctypes.c_void_p(_stream(stream))))
+
+
+def set_wait_limit(seconds: float, stream=None) -> None:
+    """Limit of the bounded device waits of the tensor-core kernels on the current device."""
+    N.check(N.lib().nedmft_set_wait_limit(float(seconds), ctypes.c_void_p(_stream(stream))))
+
+
+def wait_selftest(stream=None) -> None:
+    """One bounded wait on a barrier that nothing arrives at (then check_status raises ETIMEOUT)."""
+    N.check(N.lib().nedmft_wait_selftest(ctypes.c_void_p(_stream(stream))))
 
 
 def make_model(U: float, E: float, w1: float = 0.5, mu: float | None = None) -> N.Model:

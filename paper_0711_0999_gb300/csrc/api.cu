@@ -24,11 +24,10 @@ bool valid_contour(const nedmft_contour* c) {
 
 ModelDev model_dev(const nedmft_model& m) { return ModelDev{m.U, m.E, m.w1, isnan(m.mu) ? m.U / 2 : m.mu}; }
 
-enum class Path { Small64, Blocked64, MixedSimt, MixedUmma };
+enum class Path { Small64, Blocked64, MixedUmma };
 
 Path choose_path(const nedmft_contour& c, nedmft_precision p) {
   if (p == NEDMFT_FP64) return c.n_c <= small_path_max_n() ? Path::Small64 : Path::Blocked64;
-  if (p == NEDMFT_MIXED_FP32) return Path::MixedSimt;
   return Path::MixedUmma;
 }
 
@@ -51,7 +50,6 @@ int default_batch(const nedmft_contour& c, int nq, Path path) {
   switch (path) {
     case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
     case Path::Blocked64: per = sizeof(double2) * np * np; cap = 152; break;
-    case Path::MixedSimt: per = 3 * sizeof(float2) * np * np; cap = 64; break;
     case Path::MixedUmma: per = umma_batch_bytes_per_matrix((int)np); cap = umma_default_batch((int)np); break;
   }
   int b = (int)(budget / (per ? per : 1));
@@ -86,13 +84,6 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
       L.pbuf = align256(sizeof(double2) * kNbSimt * kNbSimt * mb);
       L.rbuf = align256(sizeof(double2) * kNbSimt * np * mb);
       L.cbuf = align256(sizeof(double2) * np * kNbSimt * mb);
-      break;
-    case Path::MixedSimt:
-      L.batch = 3 * align256(sizeof(float2) * np * np * mb);  // X', T / dX', R'
-      L.pbuf = align256(sizeof(float2) * kNbSimt * kNbSimt * mb);
-      L.rbuf = align256(sizeof(float2) * kNbSimt * np * mb);
-      L.cbuf = align256(sizeof(float2) * np * kNbSimt * mb);
-      L.extra = align256(sizeof(float2) * np * np);  // S in FP32, padded
       break;
     case Path::MixedUmma:
       L.batch = align256(umma_batch_bytes((int)np, (int)mb));
@@ -140,9 +131,6 @@ int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const doub
   const int np = L.np, mb = L.mb;
   int rc = launch_build_s(cd, sigma, S, st);
   if (rc) return rc;
-  if (L.path == Path::MixedSimt) {
-    if ((rc = launch_to_f32_padded(S, cd.n, reinterpret_cast<float2*>(extra), np, st))) return rc;
-  }
   if (L.path == Path::MixedUmma) {
     if ((rc = umma_prepare_shared(cd, S, np, eps, ebar, wq, nq, extra, st))) return rc;
   }
@@ -165,25 +153,6 @@ int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const doub
           return rc;
         if ((rc = launch_reduce<double>(cd, md, eps, ebar, wq, q0, nb, A, nullptr, np, true, first, gloc, ja, st)))
           return rc;
-        break;
-      }
-      case Path::MixedSimt: {
-        const size_t one = align256(sizeof(float2) * (size_t)np * np * mb);
-        float2* X = reinterpret_cast<float2*>(batch);
-        float2* T = reinterpret_cast<float2*>(batch + one);
-        float2* R = reinterpret_cast<float2*>(batch + 2 * one);
-        const size_t mat = (size_t)np * np;
-        if ((rc = launch_gen_a<float>(cd, md, eps, ebar, q0, nb, S, X, np, st))) return rc;
-        if ((rc = gj_blocked_simt<float>(X, cd.n, np, nb, reinterpret_cast<float2*>(pbuf), reinterpret_cast<float2*>(rbuf),
-                                         reinterpret_cast<float2*>(cbuf), status, st)))
-          return rc;
-        // T = S X' (shared S), R' = I - A' X', dX' = X' R'
-        if ((rc = gemm_simt<float>(reinterpret_cast<const float2*>(extra), np, 0, X, np, mat, T, np, mat, np, np, np, nb,
-                                   st)))
-          return rc;
-        if ((rc = launch_residual<float>(cd, md, eps, ebar, q0, nb, X, T, np, mat, R, np, st))) return rc;
-        if ((rc = gemm_simt<float>(X, np, mat, R, np, mat, T, np, mat, np, np, np, nb, st))) return rc;
-        if ((rc = launch_reduce<float>(cd, md, eps, ebar, wq, q0, nb, X, T, np, true, first, gloc, ja, st))) return rc;
         break;
       }
       case Path::MixedUmma: {
@@ -215,7 +184,7 @@ extern "C" int nedmft_g0_build(const nedmft_contour* c, const nedmft_model* m, c
 extern "C" size_t nedmft_lattice_workspace_size(const nedmft_contour* c, int32_t nq, nedmft_precision prec,
                                                 int32_t batch) {
   if (!valid_contour(c) || nq < 1) return 0;
-  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32) return 0;
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16) return 0;
   return lattice_layout(*c, nq, prec, batch).total;
 }
 
@@ -225,7 +194,7 @@ static int lattice_checks(const nedmft_contour* c, const nedmft_model* m, const 
   if (!m) return set_error(NEDMFT_EINVAL, "lattice: model is NULL");
   if (!sigma || !eps || !ebar || !wq || !ws) return set_error(NEDMFT_EINVAL, "lattice: NULL device pointer");
   if (nq < 1) return set_error(NEDMFT_EINVAL, "lattice: nq = %d < 1", nq);
-  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32)
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16)
     return set_error(NEDMFT_EINVAL, "lattice: unknown precision %d", (int)prec);
   if (((uintptr_t)ws) & 255) return set_error(NEDMFT_EINVAL, "lattice: workspace not 256-byte aligned");
   if (!(m->w1 >= 0.0 && m->w1 <= 1.0)) return set_error(NEDMFT_EINVAL, "lattice: w1 = %g outside [0, 1]", m->w1);
@@ -305,6 +274,6 @@ extern "C" int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_mod
 
 extern "C" int32_t nedmft_lattice_batch(const nedmft_contour* c, int32_t nq, nedmft_precision prec) {
   if (!valid_contour(c) || nq < 1) return 0;
-  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16 && prec != NEDMFT_MIXED_FP32) return 0;
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16) return 0;
   return lattice_layout(*c, nq, prec, 0).mb;
 }

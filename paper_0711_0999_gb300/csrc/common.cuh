@@ -42,6 +42,12 @@ void instr_end(int slot, cudaStream_t st, double flops, double bytes);  // algor
 enum DeviceStatus : int { DS_OK = 0, DS_SINGULAR = 1, DS_TIMEOUT = 2 };
 int* device_status_ptr();  // device address for the current device (cached)
 
+// Per-device launch settings, each applied once per (kernel, device) under a
+// lock: cudaFuncSetAttribute and occupancy queries act on the current device
+// only, so a process-wide "done" flag would skip them on a second GPU.
+int ensure_dyn_smem(const void* kern, int bytes);  // MaxDynamicSharedMemorySize >= bytes
+int device_sm_count(int* out);                     // multiprocessors of the current device
+
 // ------------------------------------------------------------------ complex
 
 template <class T> struct cplx;

@@ -5,49 +5,62 @@
 namespace nedmft {
 
 // ------------------------------------------------------------------ impurity step
+//
+// With S = W Sigma W, A0 = inv(G_loc) + S (Eq. effective_medium) and the
+// point-split difference D = i [M(mu - U) - M(mu)] (one entry per row:
+// D_{j,j-1} = -U W_j for j >= 1, D_{0,N-1} = +U W_0), the impurity Green's
+// function of Eq. g_imp_solve is G_imp = (1 - w1) inv(A0) + w1 inv(A0 + D).
+// Both terms share A_h = A0 + (1 - w1) D:  G_imp = inv(A0) A_h inv(A0 + D),
+// so inv(G_imp) = (A0 + D) inv(A_h) A0 and the impurity Dyson equation gives
+//   W Sigma_new W = A0 - inv(G_imp) = -w1 D + w1 (1 - w1) D inv(A_h) D,
+// two inversions (G_loc and A_h) instead of four; D inv(A_h) D is a scaled
+// gather because D is a scaled cyclic shift:
+//   (D X D)_{ij} = d_i X[i-1][j+1] d_{j+1}  (indices mod N),
+//   d_i = -U W_i (i >= 1), d_0 = +U W_0.
 
-// A0 = inv(G_loc) + W Sigma W (in place on ginv); A1 = A0 + i [M(mu-U) - M(mu)]:
-// the difference of the two point-split M matrices has -W_j U on the
-// subdiagonal (row j >= 1) and +W_0 U in the boundary element (0, N-1).
+__device__ __forceinline__ double2 d_entry(const ContourDev& c, double U, int i) {
+  const double2 w = weight(c, i);
+  return i == 0 ? make_double2(U * w.x, U * w.y) : make_double2(-U * w.x, -U * w.y);
+}
+
+// a0 <- a0 + S (a0 holds inv(G_loc)); ah = a0 + (1 - w1) D.
 __global__ void imp_build_kernel(ContourDev c, ModelDev m, const double2* __restrict__ sigma,
-                                 double2* __restrict__ a0, double2* __restrict__ a1, double2* __restrict__ x0) {
+                                 double2* __restrict__ a0, double2* __restrict__ ah) {
   const size_t total = (size_t)c.n * c.n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / c.n), j = (int)(e % c.n);
-    double2 s = cmul(cmul(weight(c, i), sigma[e]), weight(c, j));
-    double2 v = cadd(a0[e], s);
+    const int i = (int)(e / c.n), j = (int)(e % c.n);
+    const double2 s = cmul(cmul(weight(c, i), sigma[e]), weight(c, j));
+    const double2 v = cadd(a0[e], s);
     a0[e] = v;
-    x0[e] = v;
-    double2 d = make_double2(0.0, 0.0);
-    if (i >= 1 && j == i - 1) { double2 w = weight(c, i); d = make_double2(-w.x * m.U, -w.y * m.U); }
-    if (i == 0 && j == c.n - 1) { double2 w = weight(c, 0); d = cadd(d, make_double2(w.x * m.U, w.y * m.U)); }
-    a1[e] = cadd(v, d);
+    double2 h = v;
+    if (j == (i == 0 ? c.n - 1 : i - 1)) {
+      const double2 d = d_entry(c, m.U, i);
+      h = cadd(h, make_double2((1.0 - m.w1) * d.x, (1.0 - m.w1) * d.y));
+    }
+    ah[e] = h;
   }
 }
 
-// G_imp = (1 - w1) inv(A0) + w1 inv(A1)  (written to g and, if requested, gimp_out).
-__global__ void imp_mix_kernel(int n, double w1, const double2* __restrict__ x0, const double2* __restrict__ x1,
-                               double2* __restrict__ g, double2* __restrict__ gimp_out) {
+// sigma_new = W^-1 [-w1 D + w1 (1 - w1) D X_h D] W^-1 with X_h = inv(A_h); if
+// g is given, g = A0 - W sigma_new W (= inv(G_imp)).
+__global__ void imp_sigma_kernel(ContourDev c, ModelDev m, const double2* __restrict__ xh,
+                                 const double2* __restrict__ a0, double2* __restrict__ sigma_new,
+                                 double2* __restrict__ g) {
+  const int n = c.n;
   const size_t total = (size_t)n * n;
+  const double w1 = m.w1;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    double2 v = make_double2((1.0 - w1) * x0[e].x + w1 * x1[e].x, (1.0 - w1) * x0[e].y + w1 * x1[e].y);
-    g[e] = v;
-    if (gimp_out) gimp_out[e] = v;
-  }
-}
-
-// sigma_new = W^-1 (A0 - inv(G_imp)) W^-1.
-__global__ void imp_sigma_kernel(ContourDev c, const double2* __restrict__ a0, const double2* __restrict__ ginv,
-                                 double2* __restrict__ sigma_new) {
-  const size_t total = (size_t)c.n * c.n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / c.n), j = (int)(e % c.n);
-    double2 s = csub(a0[e], ginv[e]);
-    double2 wi = weight(c, i), wj = weight(c, j);
-    double2 ww = cmul(wi, wj);
-    double m2 = ww.x * ww.x + ww.y * ww.y;
-    double2 r = make_double2(ww.x / m2, -ww.y / m2);
-    sigma_new[e] = cmul(s, r);
+    const int i = (int)(e / n), j = (int)(e % n);
+    const int ip = i == 0 ? n - 1 : i - 1;  // the column of row i's entry of D
+    const int jn = j + 1 == n ? 0 : j + 1;  // the row of D whose entry lies in column j
+    const double2 di = d_entry(c, m.U, i), dj = d_entry(c, m.U, jn);
+    double2 v = cmul(cmul(di, xh[(size_t)ip * n + jn]), dj);
+    v = make_double2(w1 * (1.0 - w1) * v.x, w1 * (1.0 - w1) * v.y);
+    if (j == ip) v = make_double2(v.x - w1 * di.x, v.y - w1 * di.y);
+    if (g) g[e] = csub(a0[e], v);
+    const double2 ww = cmul(weight(c, i), weight(c, j));
+    const double m2 = ww.x * ww.x + ww.y * ww.y;
+    sigma_new[e] = cmul(v, make_double2(ww.x / m2, -ww.y / m2));
   }
 }
 
@@ -58,7 +71,7 @@ using namespace nedmft;
 extern "C" size_t nedmft_impurity_workspace_size(const nedmft_contour* c) {
   if (!c || c->n_c < 1) return 0;
   size_t n = (size_t)c->n_c;
-  return 4 * align256(sizeof(double2) * n * n) + pivot_inverse_workspace((int)n);
+  return 3 * align256(sizeof(double2) * n * n) + pivot_inverse_workspace((int)n);
 }
 
 extern "C" int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m, const nedmft_c128* gloc_d,
@@ -80,8 +93,7 @@ extern "C" int nedmft_impurity_update(const nedmft_contour* c, const nedmft_mode
   const size_t mat = align256(sizeof(double2) * (size_t)n * n);
   char* p = static_cast<char*>(ws_d);
   double2* a0 = reinterpret_cast<double2*>(p); p += mat;
-  double2* x0 = reinterpret_cast<double2*>(p); p += mat;
-  double2* a1 = reinterpret_cast<double2*>(p); p += mat;
+  double2* ah = reinterpret_cast<double2*>(p); p += mat;
   double2* g = reinterpret_cast<double2*>(p); p += mat;
   void* pws = p;
   const size_t total = (size_t)n * n;
@@ -90,14 +102,14 @@ extern "C" int nedmft_impurity_update(const nedmft_contour* c, const nedmft_mode
   NED_CUDA(cudaMemcpyAsync(a0, gloc_d, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
   int rc = pivot_inverse(a0, n, pws, st, status);  // a0 = inv(G_loc)
   if (rc) return rc;
-  imp_build_kernel<<<bx, 256, 0, st>>>(cd, md, reinterpret_cast<const double2*>(sigma_d), a0, a1, x0);
+  imp_build_kernel<<<bx, 256, 0, st>>>(cd, md, reinterpret_cast<const double2*>(sigma_d), a0, ah);
   NED_LAUNCH_CHECK("imp_build_kernel");
-  if ((rc = pivot_inverse(x0, n, pws, st, status))) return rc;  // x0 = inv(A0)
-  if ((rc = pivot_inverse(a1, n, pws, st, status))) return rc;  // a1 = inv(A1)
-  imp_mix_kernel<<<bx, 256, 0, st>>>(n, md.w1, x0, a1, g, reinterpret_cast<double2*>(gimp_d));
-  NED_LAUNCH_CHECK("imp_mix_kernel");
-  if ((rc = pivot_inverse(g, n, pws, st, status))) return rc;  // g = inv(G_imp)
-  imp_sigma_kernel<<<bx, 256, 0, st>>>(cd, a0, g, reinterpret_cast<double2*>(sigma_new_d));
+  if ((rc = pivot_inverse(ah, n, pws, st, status))) return rc;  // ah = X_h = inv(A_h)
+  imp_sigma_kernel<<<bx, 256, 0, st>>>(cd, md, ah, a0, reinterpret_cast<double2*>(sigma_new_d), gimp_d ? g : nullptr);
   NED_LAUNCH_CHECK("imp_sigma_kernel");
+  if (gimp_d) {
+    if ((rc = pivot_inverse(g, n, pws, st, status))) return rc;  // G_imp = inv(A0 - W sigma_new W)
+    NED_CUDA(cudaMemcpyAsync(gimp_d, g, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
+  }
   return NEDMFT_OK;
 }

@@ -12,6 +12,8 @@ template <class T>
 int launch_gen_a(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0, int nb,
                  const double2* S, cplx_t<T>* A, int np, cudaStream_t st);
 
+// Largest n_c of the single-CTA FP64 Gauss-Jordan path (whole matrix in shared memory).
+constexpr int kSmallPathMaxN = 112;
 int small_path_max_n();
 int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0,
                          int nb, const double2* S, double2* out, int* status, cudaStream_t st);
@@ -21,20 +23,10 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
                     int* status, cudaStream_t st);
 
 template <class T>
-int gemm_simt(const cplx_t<T>* A, int lda, size_t sa, const cplx_t<T>* B, int ldb, size_t sb, cplx_t<T>* Cout,
-              int ldc, size_t sc, int m, int n, int k, int batch, cudaStream_t st);
-
-template <class T>
-int launch_residual(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0, int nb,
-                    const cplx_t<T>* X, const cplx_t<T>* Tm, int ldt, size_t st_, cplx_t<T>* R, int np,
-                    cudaStream_t st);
-
-template <class T>
 int launch_reduce(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, const double* wq,
                   int q0, int nb, const cplx_t<T>* X, const cplx_t<T>* dX, int ldx, bool cycled, bool first,
                   double2* gloc, double2* jacc, cudaStream_t st);
 int launch_finish_current(int nt, const double2* jacc, double* j, double* ji, cudaStream_t st);
-int launch_to_f32_padded(const double2* in, int n, float2* out, int np, cudaStream_t st);
 
 // Dense FP64 inversion with partial pivoting (impurity step).
 size_t pivot_inverse_workspace(int n);

@@ -102,8 +102,6 @@ int launch_gen_a(const ContourDev& c, const ModelDev& m, const double* eps, cons
 }
 template int launch_gen_a<double>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
                                   const double2*, double2*, int, cudaStream_t);
-template int launch_gen_a<float>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
-                                 const double2*, float2*, int, cudaStream_t);
 
 // ------------------------------------------------------------------ record a device failure
 
@@ -172,16 +170,13 @@ __global__ void __launch_bounds__(512) gj_small_fp64_kernel(ContourDev c, ModelD
   }
 }
 
-int small_path_max_n() { return 112; }
+int small_path_max_n() { return kSmallPathMaxN; }
 
 int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0,
                          int nb, const double2* S, double2* out, int* status, cudaStream_t st) {
   size_t smem = (size_t)(c.n * c.n + c.n) * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    NED_CUDA(cudaFuncSetAttribute(gj_small_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
-  }
+  int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_small_fp64_kernel), 227 * 1024);
+  if (rc) return rc;
   gj_small_fp64_kernel<<<nb, 512, smem, st>>>(c, m, eps, ebar, q0, S, out, status);
   NED_LAUNCH_CHECK("gj_small_fp64_kernel");
   return NEDMFT_OK;
@@ -325,7 +320,6 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
   return NEDMFT_OK;
 }
 template int gj_blocked_simt<double>(double2*, int, int, int, double2*, double2*, double2*, int*, cudaStream_t);
-template int gj_blocked_simt<float>(float2*, int, int, int, float2*, float2*, float2*, int*, cudaStream_t);
 
 // ------------------------------------------------------------------ FP64 inversion with partial pivoting
 
@@ -536,12 +530,10 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   NED_LAUNCH_CHECK("pad_identity_kernel");
   const size_t upd_smem = sizeof(double2) * (64 * (NB + 1) + NB * 64);
   const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
-  static bool attr = false;
-  if (!attr) {
-    NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<double, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)upd_smem));
-    NED_CUDA(cudaFuncSetAttribute(tour_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tour_smem));
-    attr = true;
+  {
+    int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<double, NB>), (int)upd_smem);
+    if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem);
+    if (rc) return rc;
   }
   for (int k0 = 0; k0 < n; k0 += NB) {
     // tournament rounds over the rows k0 .. n-1
@@ -574,120 +566,6 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   NED_LAUNCH_CHECK("unpermute_kernel");
   return NEDMFT_OK;
 }
-
-// ------------------------------------------------------------------ batched complex GEMM, CUDA cores
-
-// Cout[b] = A[b] (m x k) * B[b] (k x n), all row-major with the given leading
-// dimensions and batch strides (stride 0 shares an operand).  m, n multiples
-// of 64, k a multiple of 32.
-template <class T>
-__global__ void __launch_bounds__(256) gemm_simt_kernel(const cplx_t<T>* __restrict__ A, int lda, size_t sa,
-                                                        const cplx_t<T>* __restrict__ B, int ldb, size_t sb,
-                                                        cplx_t<T>* __restrict__ Cout, int ldc, size_t sc, int k) {
-  using C = cplx_t<T>;
-  constexpr int TM = 64, TN = 64, TK = 32;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C (*as_)[TK + 1] = reinterpret_cast<C (*)[TK + 1]>(smraw);
-  C (*bs_)[TN] = reinterpret_cast<C (*)[TN]>(smraw + sizeof(C) * TM * (TK + 1));
-  const int b = blockIdx.z;
-  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
-  const C* a = A + b * sa;
-  const C* bm = B + b * sb;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  C acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = mk<T>(0, 0);
-  for (int kb = 0; kb < k; kb += TK) {
-    for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) as_[e / TK][e % TK] = a[(size_t)(i0 + e / TK) * lda + kb + e % TK];
-    for (int e = threadIdx.x; e < TK * TN; e += blockDim.x) bs_[e / TN][e % TN] = bm[(size_t)(kb + e / TN) * ldb + j0 + e % TN];
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < TK; ++kk) {
-      C av[4], bv[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = as_[ty + 16 * r][kk];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = bs_[kk][tx + 16 * q];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cfma(acc[r][q], av[r], bv[q]);
-    }
-    __syncthreads();
-  }
-  C* cm = Cout + b * sc;
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cm[(size_t)(i0 + ty + 16 * r) * ldc + j0 + tx + 16 * q] = acc[r][q];
-}
-
-template <class T>
-int gemm_simt(const cplx_t<T>* A, int lda, size_t sa, const cplx_t<T>* B, int ldb, size_t sb, cplx_t<T>* Cout,
-              int ldc, size_t sc, int m, int n, int k, int batch, cudaStream_t st) {
-  if (m % 64 || n % 64 || k % 32) return set_error(NEDMFT_EINVAL, "gemm_simt: bad shape %d x %d x %d", m, n, k);
-  const size_t smem = sizeof(cplx_t<T>) * (64 * 33 + 32 * 64);
-  NED_CUDA(cudaFuncSetAttribute(gemm_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  gemm_simt_kernel<T><<<dim3(n / 64, m / 64, batch), 256, smem, st>>>(A, lda, sa, B, ldb, sb, Cout, ldc, sc, k);
-  NED_LAUNCH_CHECK("gemm_simt_kernel");
-  return NEDMFT_OK;
-}
-template int gemm_simt<float>(const float2*, int, size_t, const float2*, int, size_t, float2*, int, size_t, int, int,
-                              int, int, cudaStream_t);
-template int gemm_simt<double>(const double2*, int, size_t, const double2*, int, size_t, double2*, int, size_t, int,
-                               int, int, int, cudaStream_t);
-
-// ------------------------------------------------------------------ refinement residual
-
-// R'[b] = I - A'_q X'[b] with A'_q = P (B_q - S):
-//   R'[r][j] = delta_rj - (B_q X')[i][j] + T[b][i][j],  i = row of A_q behind row r,
-// where T = S X' (computed by a GEMM, any precision) and (B_q X')[i][j] uses
-// the bidiagonal entries of B_q in FP64.  Rows/columns >= N: R' = I - X'.
-template <class T>
-__global__ void residual_kernel(ContourDev c, ModelDev m, const double* __restrict__ eps_d,
-                                const double* __restrict__ ebar_d, int q0, const cplx_t<T>* __restrict__ X,
-                                const cplx_t<T>* __restrict__ Tm, int ldt, size_t st_, cplx_t<T>* __restrict__ R,
-                                int np) {
-  const int b = blockIdx.y;
-  const double eps = eps_d[q0 + b], ebar = ebar_d[q0 + b];
-  const bool sh = shifted_point(m, eps);
-  const cplx_t<T>* x = X + (size_t)b * np * np;
-  const cplx_t<T>* t = Tm + b * st_;
-  cplx_t<T>* out = R + (size_t)b * np * np;
-  const size_t total = (size_t)np * np;
-  const double2 bdiag = make_double2(0.0, 1.0);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(e / np), j = (int)(e % np);
-    double2 v = make_double2(r == j ? 1.0 : 0.0, 0.0);
-    if (r < c.n) {
-      int i = sh ? (r + 1 == c.n ? 0 : r + 1) : r;
-      double2 bx = cmul(bdiag, to_d(x[(size_t)i * np + j]));
-      if (i >= 1) bx = cadd(bx, cmul(b_sub(c, m, eps, ebar, i), to_d(x[(size_t)(i - 1) * np + j])));
-      if (i == 0) bx = cadd(bx, cmul(b_corner(c, m, eps), to_d(x[(size_t)(c.n - 1) * np + j])));
-      v = csub(v, bx);
-      v = cadd(v, to_d(t[(size_t)i * ldt + j]));
-    } else {
-      v = csub(v, to_d(x[(size_t)r * np + j]));
-    }
-    out[e] = cvt<T>(v);
-  }
-}
-
-template <class T>
-int launch_residual(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar, int q0, int nb,
-                    const cplx_t<T>* X, const cplx_t<T>* Tm, int ldt, size_t st_, cplx_t<T>* R, int np,
-                    cudaStream_t st) {
-  size_t total = (size_t)np * np;
-  int bx = (int)((total + 255) / 256);
-  if (bx > 2048) bx = 2048;
-  residual_kernel<T><<<dim3(bx, nb), 256, 0, st>>>(c, m, eps, ebar, q0, X, Tm, ldt, st_, R, np);
-  NED_LAUNCH_CHECK("residual_kernel");
-  return NEDMFT_OK;
-}
-template int launch_residual<float>(const ContourDev&, const ModelDev&, const double*, const double*, int, int,
-                                    const float2*, const float2*, int, size_t, float2*, int, cudaStream_t);
 
 // ------------------------------------------------------------------ FP64 reductions over the points
 
@@ -770,34 +648,10 @@ int launch_reduce(const ContourDev& c, const ModelDev& m, const double* eps, con
 template int launch_reduce<double>(const ContourDev&, const ModelDev&, const double*, const double*, const double*,
                                    int, int, const double2*, const double2*, int, bool, bool, double2*, double2*,
                                    cudaStream_t);
-template int launch_reduce<float>(const ContourDev&, const ModelDev&, const double*, const double*, const double*,
-                                  int, int, const float2*, const float2*, int, bool, bool, double2*, double2*,
-                                  cudaStream_t);
 
 int launch_finish_current(int nt, const double2* jacc, double* j, double* ji, cudaStream_t st) {
   finish_current_kernel<<<ceil_div(nt, 128), 128, 0, st>>>(nt, jacc, j, ji);
   NED_LAUNCH_CHECK("finish_current_kernel");
-  return NEDMFT_OK;
-}
-
-// ------------------------------------------------------------------ conversions
-
-__global__ void to_f32_kernel(const double2* __restrict__ in, int n, int ldi, float2* __restrict__ out, int ldo,
-                              int rows_out, int cols_out) {
-  const size_t total = (size_t)rows_out * cols_out;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / cols_out), j = (int)(e % cols_out);
-    double2 v = (i < n && j < n) ? in[(size_t)i * ldi + j] : make_double2(0.0, 0.0);
-    out[(size_t)i * ldo + j] = make_float2((float)v.x, (float)v.y);
-  }
-}
-
-int launch_to_f32_padded(const double2* in, int n, float2* out, int np, cudaStream_t st) {
-  size_t total = (size_t)np * np;
-  int bx = (int)((total + 255) / 256);
-  if (bx > 4096) bx = 4096;
-  to_f32_kernel<<<bx, 256, 0, st>>>(in, n, n, out, np, np, np);
-  NED_LAUNCH_CHECK("to_f32_kernel");
   return NEDMFT_OK;
 }
 

@@ -7,7 +7,8 @@
 namespace nedmft {
 namespace {
 
-constexpr int kStaticMaxN = 112;   // largest n_c (the single-CTA FP64 Gauss-Jordan path)
+constexpr int kStaticMaxN = kSmallPathMaxN;  // largest n_c (the single-CTA FP64 Gauss-Jordan path)
+static_assert(kStaticMaxN == 112, "the documented limit of nedmft_lattice_gloc_static");
 constexpr int kStaticBatch = 32;   // points inverted per pass
 constexpr size_t kStaticS = (size_t)kStaticMaxN * kStaticMaxN * sizeof(double2);
 constexpr size_t kStaticBatchBytes = (size_t)kStaticBatch * kStaticMaxN * kStaticMaxN * sizeof(double2);
@@ -52,7 +53,7 @@ extern "C" int nedmft_lattice_gloc_static(const nedmft_contour* c, const nedmft_
     return set_error(NEDMFT_EINVAL, "lattice_gloc_static: NULL argument");
   if (c->n_t < 1 || c->n_tau < 1 || c->n_c != 2 * c->n_t + c->n_tau)
     return set_error(NEDMFT_EINVAL, "lattice_gloc_static: invalid contour");
-  if (c->n_c > kStaticMaxN)
+  if (c->n_c > kStaticMaxN || c->n_c > small_path_max_n())
     return set_error(NEDMFT_EINVAL, "lattice_gloc_static: n_c = %d exceeds the static scratch limit of %d", c->n_c,
                      kStaticMaxN);
   if (nq < 1) return set_error(NEDMFT_EINVAL, "lattice_gloc_static: nq = %d < 1", nq);

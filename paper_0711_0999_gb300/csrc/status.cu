@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace nedmft {
 
@@ -85,6 +86,34 @@ int* device_status_ptr() {
   return g_status_addr[dev];
 }
 
+namespace {
+std::mutex g_attr_mu;
+std::vector<std::pair<const void*, int>> g_attr_done[kMaxDevices];  // (kernel, bytes) per device
+int g_sm_count[kMaxDevices] = {0};
+}  // namespace
+
+int ensure_dyn_smem(const void* kern, int bytes) {
+  int dev = 0;
+  NED_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(NEDMFT_ECUDA, "device %d beyond the library's table", dev);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const auto& e : g_attr_done[dev])
+    if (e.first == kern && e.second >= bytes) return NEDMFT_OK;
+  NED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_attr_done[dev].emplace_back(kern, bytes);
+  return NEDMFT_OK;
+}
+
+int device_sm_count(int* out) {
+  int dev = 0;
+  NED_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(NEDMFT_ECUDA, "device %d beyond the library's table", dev);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (!g_sm_count[dev]) NED_CUDA(cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev));
+  *out = g_sm_count[dev];
+  return NEDMFT_OK;
+}
+
 }  // namespace nedmft
 
 using namespace nedmft;
@@ -149,4 +178,16 @@ extern "C" int nedmft_instrument_read(int64_t* launches, int64_t* timed_launches
   if (timed_flops) *timed_flops = fl;
   if (timed_bytes) *timed_bytes = by;
   return NEDMFT_OK;
+}
+
+extern "C" int nedmft_set_wait_limit(double seconds, void* stream) {
+  if (!(seconds >= 0.0 && seconds <= 60.0))
+    return set_error(NEDMFT_EINVAL, "set_wait_limit: %g s outside [0, 60]", seconds);
+  return umma_set_wait_ns((uint64_t)(seconds * 1e9), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int nedmft_wait_selftest(void* stream) {
+  int* p = device_status_ptr();
+  if (!p) return set_error(NEDMFT_ECUDA, "cannot locate the device status word");
+  return umma_wait_selftest(p, static_cast<cudaStream_t>(stream));
 }

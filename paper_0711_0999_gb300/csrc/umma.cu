@@ -73,6 +73,13 @@ struct Split3 {
   __device__ static int b(int p) { return p == 1 ? 1 : 0; }
 };
 
+// hi*hi alone: for a product whose own rounding lies far below the target.
+struct Split1 {
+  static constexpr int kPairs = 1;
+  __device__ static int a(int) { return 0; }
+  __device__ static int b(int) { return 0; }
+};
+
 template <class C, class Pairs, class Epi>
 __device__ __forceinline__ void umma_gemm_body(const GemmParams& p, const Epi& epi) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -127,7 +134,7 @@ __device__ __forceinline__ void umma_gemm_body(const GemmParams& p, const Epi& e
         const int s = kt % C::kStages;
         const uint32_t ph = (kt / C::kStages) & 1;
         uint64_t t0 = global_ns();
-        while (!mbar_test(&full[s], ph) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_test(&full[s], ph) && global_ns() - t0 < kDrainNs) {
         }
       }
     }
@@ -175,7 +182,7 @@ __device__ __forceinline__ void umma_gemm_body(const GemmParams& p, const Epi& e
   if (warp == 1) {
     // the tensor core must be idle before the columns are released
     uint64_t t0 = global_ns();
-    while (!mbar_test(acc_full, 0) && global_ns() - t0 < kWaitNs) {
+    while (!mbar_test(acc_full, 0) && global_ns() - t0 < kDrainNs) {
     }
     tc_fence_after();
     tmem_dealloc(tmem, C::kTmemCols);
@@ -192,6 +199,7 @@ __global__ void __launch_bounds__(192, 1) umma_gemm_flag_kernel(GemmParams p, Ep
 
 
 using CfgGJ = Cfg<256, 2, 2, 2>;  // 128 x 256 tiles, hi/lo operands, 2 stages (192 KB)
+using CfgHi = Cfg<256, 1, 1, 4>;  // 128 x 256 tiles, hi operands only, 4 stages (192 KB)
 
 // Stages of half tiles (32 k): 4 x 48 KB for the persistent Gauss-Jordan products.
 template <int BN, int SA, int SB, int STAGES>
@@ -203,15 +211,16 @@ struct CfgHalf {
   static constexpr int kBTiles = BN / kTileRows;
   static constexpr int kHalfBytes = kTileBytes / 2;
   static constexpr int kStageBytes = (SA + SB * kBTiles) * kHalfBytes;
-  static constexpr int kSmem = STAGES * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kBarBytes = 512;
+  static constexpr int kSmem = STAGES * kStageBytes + 1024 /*align*/ + kBarBytes;
 };
 using CfgGJH = CfgHalf<256, 2, 2, 4>;
 
-// Persistent form: CTA (or CTA pair) c takes tiles c, c + G, c + 2G, ... of
-// the linear order (batch, m tile, n tile), n fastest, so that at any time the
-// CTAs work on about one matrix and its operand panels stay in L2.  The stage
-// ring runs on across tiles and the TMEM holds two accumulators, so the
-// epilogue of one tile overlaps the loads and products of the next.
+// Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear
+// order (batch, m tile, n tile), n fastest, so that at any time the CTAs work
+// on about one matrix and its operand panels stay in L2.  The stage ring runs
+// on across tiles and the TMEM holds two accumulators, so the epilogue of one
+// tile overlaps the loads and products of the next.
 //
 // Epilogues with Epi::kStage stage -acc of plain tiles in shared memory, one
 // 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, kRedBuf
@@ -219,56 +228,62 @@ using CfgGJH = CfgHalf<256, 2, 2, 4>;
 // reduction per box through Epi::red_map.
 constexpr int kRedBuf = 2;
 constexpr int kRedBox = 32 * 32 * 4;
+constexpr int kMaxBoxBars = 16;
 template <int EPIW>
-constexpr int red_stage_bytes() { return 768 + EPIW * kRedBuf * kRedBox; }
+constexpr int red_stage_bytes() { return 512 + EPIW * kRedBuf * kRedBox; }
 
-// PAIR = 2: clusters of two CTAs take m tiles 2j and 2j+1 of the same n tile;
-// each loads its own A and half of B, multicast to both, and a stage is
-// refilled only when both CTAs' products have released it.
-template <class C, class Pairs, class Epi, int EPIW, int PAIR>
+// The barriers and flags of a persistent kernel, after its stage ring.
+template <int STAGES>
+struct PersistBars {
+  uint64_t full[STAGES], empty[STAGES];  // stage filled / stage released by the products
+  uint64_t acc_full[2], acc_empty[2];    // accumulator buffer ready / drained
+  uint64_t drain;                        // every product issued by this CTA has completed
+  uint64_t box[kMaxBoxBars];             // staging-box loads of the epilogue warps
+  uint32_t tmem_slot;
+  int abort;
+};
+
+template <class C, class Pairs, class Epi, int EPIW>
 __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     umma_gemm_persistent_kernel(const __grid_constant__ TileMapParams p, const __grid_constant__ Epi epi, int n_tiles,
                                 int m_tiles, int batch) {
+  static_assert(sizeof(PersistBars<C::kStages>) <= C::kBarBytes, "barrier block");
+  static_assert(EPIW * kRedBuf <= kMaxBoxBars, "staging-box barriers");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
-  uint64_t* empty = full + C::kStages;
-  uint64_t* acc_full = empty + C::kStages;  // 2
-  uint64_t* acc_empty = acc_full + 2;       // 2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto& bars = *reinterpret_cast<PersistBars<C::kStages>*>(smem + C::kStages * C::kStageBytes);
+  uint64_t* full = bars.full;
+  uint64_t* empty = bars.empty;
+  uint64_t* acc_full = bars.acc_full;
+  uint64_t* acc_empty = bars.acc_empty;
+  volatile int* abort_flag = &bars.abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // work units: (batch entry, pair of m tiles, n tile) for PAIR = 2
-  const int per_u = n_tiles * (m_tiles / PAIR);
+  const int per_u = n_tiles * m_tiles;
   const int total = per_u * batch;
-  const int G = gridDim.x / PAIR;
-  const int cta = blockIdx.x / PAIR;
-  const int rank = PAIR == 2 ? (int)cluster_ctarank() : 0;
-  constexpr uint16_t kBoth = 3;
+  const int G = gridDim.x;
+  const int cta = blockIdx.x;
   constexpr uint32_t kCols = 2 * C::kBn;  // two accumulators
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], PAIR);
+      mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
       mbar_init(&acc_empty[s], 32 * EPIW);
     }
-    if (Epi::kStage) {
-      uint64_t* box_bar = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + 128);
-      for (int k = 0; k < EPIW * kRedBuf; ++k) mbar_init(&box_bar[k], 1);
-    }
+    mbar_init(&bars.drain, 1);
+    if (Epi::kStage)
+      for (int k = 0; k < EPIW * kRedBuf; ++k) mbar_init(&bars.box[k], 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(tmem_slot, kCols);
+  if (warp == 1) tmem_alloc(&bars.tmem_slot, kCols);
   tc_fence_before();
   __syncthreads();
-  if constexpr (PAIR == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = bars.tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -276,7 +291,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       bool ok = true;
       for (int t = cta; t < total && ok; t += G) {
         const int b = t / per_u, rem = t % per_u;
-        const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
+        const int mt = rem / n_tiles, nt = rem % n_tiles;
         const long long a0 = p.a + b * p.a_batch + (long long)mt * p.kt;
         const long long b0 = p.b + b * p.b_batch + (long long)nt * C::kBTiles * p.kt;
         for (int h = 0; h < 2 * p.kt; ++h, ++it) {  // half tiles: kt = h / 2, core columns 4 (h % 2) .. +3
@@ -289,22 +304,15 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
           for (int sa = 0; sa < C::kSa; ++sa)
             tma_load_4d(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), &full[s]);
           for (int sb = 0; sb < C::kSb; ++sb)
-            for (int u = 0; u < C::kBTiles; ++u) {
-              const int idx = sb * C::kBTiles + u;
-              unsigned char* dst = st + (C::kSa + idx) * C::kHalfBytes;
-              const int L = (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt);
-              if constexpr (PAIR == 2) {
-                if ((idx & 1) == rank) tma_load_4d_mc(&p.map, dst, 0, kc, 0, L, &full[s], kBoth);
-              } else {
-                tma_load_4d(&p.map, dst, 0, kc, 0, L, &full[s]);
-              }
-            }
+            for (int u = 0; u < C::kBTiles; ++u)
+              tma_load_4d(&p.map, st + (C::kSa + sb * C::kBTiles + u) * C::kHalfBytes, 0, kc, 0,
+                          (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt), &full[s]);
         }
       }
       // no copy may be left in flight at exit
       for (int k = it - C::kStages < 0 ? 0 : it - C::kStages; k < it; ++k) {
         const uint64_t t0 = global_ns();
-        while (!mbar_test(&full[k % C::kStages], (k / C::kStages) & 1) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_test(&full[k % C::kStages], (k / C::kStages) & 1) && global_ns() - t0 < kDrainNs) {
         }
       }
     }
@@ -336,11 +344,12 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
                        (h > 0 || kk > 0 || q > 0) ? 1u : 0u);
             }
           }
-          if constexpr (PAIR == 2) mma_commit_mc(&empty[s], kBoth);
-          else mma_commit(&empty[s]);
+          mma_commit(&empty[s]);
         }
-        mma_commit(&acc_full[buf]);
+        if (ok) mma_commit(&acc_full[buf]);
       }
+      // completes when every product issued above has (also after an abort)
+      mma_commit(&bars.drain);
     }
   } else {
     // EPIW epilogue warps: warp w owns TMEM lanes 32 (w % 4) .. +31 and one of
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     // staging boxes start 1 KB after the barrier block (1024-byte aligned for
     // the swizzle); box k of this warp has the load barrier box_bar[k]
     unsigned char* red_stage = smem + C::kStages * C::kStageBytes + 1024 + (warp - 2) * kRedBuf * kRedBox;
-    uint64_t* box_bar = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + 128) + (warp - 2) * kRedBuf;
+    uint64_t* box_bar = bars.box + (warp - 2) * kRedBuf;
     uint32_t box_phase = 0;    // bit k: parity of box_bar[k]'s next completion
     uint32_t box_loading = 0;  // bit k: a load into box k is in flight
     int nred = 0;
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     bool ok = true;
     for (int t = cta; t < total && ok; t += G, ++lt) {
       const int b = t / per_u, rem = t % per_u;
-      const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
+      const int mt = rem / n_tiles, nt = rem % n_tiles;
       const int buf = lt & 1;
       const int md = epi.mode(mt, nt);
       const int row = q * 32 + lane;
@@ -444,14 +453,17 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     for (int k = 0; k < kRedBuf; ++k) {
       if (!(box_loading >> k & 1)) continue;
       const uint64_t t0 = global_ns();
-      while (!mbar_test(&box_bar[k], (box_phase >> k) & 1) && global_ns() - t0 < kWaitNs) {
+      while (!mbar_test(&box_bar[k], (box_phase >> k) & 1) && global_ns() - t0 < kDrainNs) {
       }
     }
     if (Epi::kStage) bulk_wait_all();
   }
   __syncthreads();
-  if constexpr (PAIR == 2) cluster_sync();  // no multicast into a CTA that has left
   if (warp == 1) {
+    // the tensor core must be idle before the columns are released
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(&bars.drain, 0) && global_ns() - t0 < kDrainNs) {
+    }
     tc_fence_after();
     tmem_dealloc(tmem, kCols);
   }
@@ -463,52 +475,17 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
                            cudaStream_t st) {
   const int smem_bytes = C::kSmem + (Epi::kStage ? red_stage_bytes<EPIW>() : 0);
   const dim3 block(64 + 32 * EPIW);
-  if (m_tiles % 2 == 0) {
-    // clusters of two CTAs sharing B; as many clusters as fit at once
-    auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 2>;
-    static int max_clusters = 0;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem_bytes;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (!max_clusters) {
-      NED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
-      cfg.gridDim = dim3(2);
-      NED_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
-      if (max_clusters < 1) return set_error(NEDMFT_ECUDA, "persistent GEMM: no cluster of 2 fits on this device");
-    }
-    const int units = n_tiles * (m_tiles / 2) * batch;
-    cfg.gridDim = dim3(2 * (units < max_clusters ? units : max_clusters));
-    NED_CUDA(cudaLaunchKernelEx(&cfg, kern, p, epi, n_tiles, m_tiles, batch));
-    NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
-    return NEDMFT_OK;
-  }
-  auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 1>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    NED_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
-    attr_set = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    NED_CUDA(cudaGetDevice(&dev));
-    NED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>;
+  int rc = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem_bytes);
+  int sms = 0;
+  if (!rc) rc = device_sm_count(&sms);
+  if (rc) return rc;
   const int total = n_tiles * m_tiles * batch;
   const int grid = total < sms ? total : sms;
   kern<<<grid, block, smem_bytes, st>>>(p, epi, n_tiles, m_tiles, batch);
   NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
   return NEDMFT_OK;
 }
-
 
 
 // ------------------------------------------------------------------ epilogues
@@ -1186,12 +1163,7 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
     __nv_bfloat16* nxt_c = cimg + ((step + 1) & 1) * chalf;
     __nv_bfloat16* nxt_t = timg + ((step + 1) & 1) * thalf;
     if constexpr (W == 128) {
-      static bool attr = false;
-      if (!attr) {
-        NED_CUDA(cudaFuncSetAttribute(gj_pivot_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kPivSmem));
-        attr = true;
-      }
+      if (int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_pivot_pack_kernel), (int)kPivSmem)) return rc;
       gj_pivot_pack_kernel<<<nb, 1024, kPivSmem, st>>>(A, np, k0, pimg, pstride, pslice, status);
       NED_LAUNCH_CHECK("gj_pivot_pack_kernel");
     } else {
@@ -1562,31 +1534,33 @@ constexpr int kOzEpiW = 8;                     // epilogue warps: two per TMEM l
 constexpr int kOzEpiCols = kOzBn * 4 / kOzEpiW;  // accumulator columns per epilogue thread
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 
-// Persistent, in clusters of two CTAs: the units (refined matrix, m tile, pair
-// of n tiles), m fastest, are dealt round-robin to the clusters; CTA r of a
-// cluster takes n tile 2 j + r, so both multiply the same rows of S_d: each
-// loads half of the A slices, multicast to both, and its own B half tile, and a
-// stage is refilled only when both CTAs' products have released it.
-// Consecutive units share the B tile and all share A (S_d), which stays in L2.
-// Chunks of kOzChunkKt K tiles alternate between two TMEM buffers of kOzS
-// accumulators of kOzBn columns across units, so the epilogue drains (and
-// finishes a unit) while the next chunk is multiplied.
+// Persistent: the units (refined matrix, m tile, n tile), m fastest, are
+// dealt round-robin to the CTAs.  Consecutive units share the B tile and all
+// share A (S_d), which stays in L2.  Chunks of kOzChunkKt K tiles alternate
+// between two TMEM buffers of kOzS accumulators of kOzBn columns across units,
+// so the epilogue drains (and finishes a unit) while the next chunk is
+// multiplied.
+struct OzBars {
+  uint64_t full[kOzStages], empty[kOzStages], acc_full[2], acc_empty[2], drain;
+  uint32_t tmem_slot;
+  int abort;
+};
+static_assert(sizeof(OzBars) <= 256, "residual barrier block");
+
 __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
-  uint64_t* empty = full + kOzStages;
-  uint64_t* acc_full = empty + kOzStages;  // 2 buffers
-  uint64_t* acc_empty = acc_full + 2;      // 2 buffers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  OzBars& bars = *reinterpret_cast<OzBars*>(smem + kOzStages * kOzStageBytes);
+  uint64_t* full = bars.full;
+  uint64_t* empty = bars.empty;
+  uint64_t* acc_full = bars.acc_full;
+  uint64_t* acc_empty = bars.acc_empty;
+  volatile int* abort_flag = &bars.abort;
   __shared__ int refined[kRedMaxBatch];
   __shared__ int n_refined;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tiles = p.np / kTileRows, n_pairs = p.np / kOzBn;  // 2 np / kOzBn n tiles, in pairs
-  const int per = m_tiles * n_pairs;
-  const int rank = (int)cluster_ctarank();
-  constexpr uint16_t kBoth = 3;
+  const int m_tiles = p.np / kTileRows, n_tiles = 2 * p.np / kOzBn;
+  const int per = m_tiles * n_tiles;
   const int kh = 2 * p.kt;                  // half tiles per unit
   const int hc = 2 * kOzChunkKt;            // half tiles per chunk
   const int nchunks = (kh + hc - 1) / hc;   // chunks per unit
@@ -1594,12 +1568,13 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
   if (threadIdx.x == 0) {
     for (int s = 0; s < kOzStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);
+      mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
       mbar_init(&acc_empty[s], 32 * kOzEpiW);
     }
+    mbar_init(&bars.drain, 1);
     *abort_flag = 0;
     fence_barrier_init();
     int r = 0;
@@ -1607,14 +1582,13 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
       if (p.flags[p.q0 + b]) refined[r++] = b;
     n_refined = r;
   }
-  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  if (warp == 1) tmem_alloc(&bars.tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = bars.tmem_slot;
   const int units = n_refined * per;
-  const int G = gridDim.x / 2, cl = blockIdx.x / 2;
+  const int G = gridDim.x, cl = blockIdx.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1622,10 +1596,11 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
       bool ok = true;
       for (int u = cl; u < units && ok; u += G) {
         const int bidx = refined[u / per], rem = u % per;
-        const int mt = rem % m_tiles, ntp = rem / m_tiles;
+        const int mt = rem % m_tiles, nt = rem / m_tiles;
         const long long a0 = (long long)mt * p.kt;
-        const long long b0 = bidx * p.b_batch + (long long)ntp * p.kt;
-        const int rg = 8 * rank;  // B rows (2 ntp + rank) * 64 .. +63: row groups 8 rank .. +7 of tile ntp
+        // B rows nt * 64 .. +63: row groups 8 (nt & 1) .. +7 of tile nt / 2
+        const long long b0 = bidx * p.b_batch + (long long)(nt >> 1) * p.kt;
+        const int rg = 8 * (nt & 1);
         for (int h = 0; h < kh; ++h, ++it) {
           const int s = it % kOzStages;
           const uint32_t ph = (it / kOzStages) & 1;
@@ -1633,8 +1608,8 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
           unsigned char* st = smem + s * kOzStageBytes;
           const int kt = h >> 1, kc = 4 * (h & 1);
           mbar_arrive_expect_tx(&full[s], kOzStageBytes);
-          for (int sl = rank * (kOzS / 2); sl < (rank + 1) * (kOzS / 2); ++sl)
-            tma_load_4d_mc(&p.a_map, st + sl * kOzHalfA, 0, kc, 0, (int)(a0 + sl * p.a_slice + kt), &full[s], kBoth);
+          for (int sl = 0; sl < kOzS; ++sl)
+            tma_load_4d(&p.a_map, st + sl * kOzHalfA, 0, kc, 0, (int)(a0 + sl * p.a_slice + kt), &full[s]);
           for (int sl = 0; sl < kOzS; ++sl)
             tma_load_4d(&p.b_map, st + kOzS * kOzHalfA + sl * kOzHalfB, 0, kc, rg, (int)(b0 + sl * p.b_slice + kt),
                         &full[s]);
@@ -1643,7 +1618,7 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
       // no copy may be left in flight at exit
       for (int k = it - kOzStages < 0 ? 0 : it - kOzStages; k < it; ++k) {
         const uint64_t t0 = global_ns();
-        while (!mbar_test(&full[k % kOzStages], (k / kOzStages) & 1) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_test(&full[k % kOzStages], (k / kOzStages) & 1) && global_ns() - t0 < kDrainNs) {
         }
       }
     }
@@ -1677,17 +1652,15 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
                        idesc_bf16(128, (kOzS - a) * kOzBn), (first && kk == 0 && a == 0) ? 0u : 1u);
             }
           }
-          mma_commit_mc(&empty[s], kBoth);
+          mma_commit(&empty[s]);
           if ((h % hc) == hc - 1 || h == kh - 1) {
             mma_commit(&acc_full[buf]);
             ++cg;
           }
         }
       }
-      if (!ok) {
-        mma_commit(&acc_full[0]);
-        mma_commit(&acc_full[1]);
-      }
+      // completes when every product issued above has (also after an abort)
+      mma_commit(&bars.drain);
     }
   } else {
     // kOzEpiW epilogue warps: warp w owns TMEM lanes 32 (w % 4) .. +31 (rows of
@@ -1699,7 +1672,7 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
     int cg = 0;
     for (int u = cl; u < units && ok; u += G) {
       const int bidx = refined[u / per], rem = u % per;
-      const int mt = rem % m_tiles, nt = 2 * (rem / m_tiles) + rank;
+      const int mt = rem % m_tiles, nt = rem / m_tiles;
       const int i = mt * kTileRows + row;  // output row of S_d X'
       const int n = p.c.n, np = p.np;
       const bool sh = shifted_point(p.m, p.eps[p.q0 + bidx]);
@@ -1794,19 +1767,10 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
   }
   __syncthreads();
   if (warp == 1) {
-    // every MMA of this CTA (and so its releases of the peer's stages) has
-    // completed before the cluster is left and the TMEM is released
-    const int mine = (units - cl + G - 1) / G > 0 ? (units - cl + G - 1) / G : 0;
-    const int chunks = mine * nchunks;
-    for (int s = 0; s < 2 && s < chunks; ++s) {
-      const int last = ((chunks - 1 - s) / 2) * 2 + s;  // last chunk that used buffer s
-      const uint64_t t0 = global_ns();
-      while (!mbar_test(&acc_full[s], (last >> 1) & 1) && global_ns() - t0 < kWaitNs) {
-      }
+    // the tensor core must be idle before the columns are released
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(&bars.drain, 0) && global_ns() - t0 < kDrainNs) {
     }
-  }
-  cluster_sync();  // no multicast or release into a CTA that has left
-  if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -1814,16 +1778,49 @@ __global__ void __launch_bounds__(64 + 32 * kOzEpiW, 1) oz_residual_kernel(const
 }
 
 // dX' = acc (FP32 interleaved).
+// and its bf16 image as the A operand of the second-order term dX' R' (row i,
+// k = 2j, 2j+1: the 32 values of a chunk are 32 consecutive k, four 16-byte
+// core-matrix rows).
 struct EpiStore {
+  float* out;
+  size_t bstride;  // floats between matrices
+  int np;
+  __nv_bfloat16* img;
+  size_t img_stride;  // elements between matrices
+  __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
+    const int i = mt * kTileRows + r;
+    const int k0 = nt * CfgGJ::kBn + c0;
+    float* row = out + b * bstride + (size_t)i * 2 * np + k0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      *reinterpret_cast<float4*>(row + 4 * u) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    __nv_bfloat16* im = img + b * img_stride;
+    const int kt = 2 * np / kTileK;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        h[e] = bf2_bits(__float2bfloat16_rn(v[8 * g + 2 * e]), __float2bfloat16_rn(v[8 * g + 2 * e + 1]));
+      *reinterpret_cast<uint4*>(im + img_offset(i, k0 + 8 * g, kt)) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  }
+};
+
+// dX' += acc (FP32 interleaved): the second-order term of the refinement.
+struct EpiAdd {
   float* out;
   size_t bstride;  // floats between matrices
   int np;
   __device__ void operator()(int b, int mt, int nt, int r, int c0, const float* v) const {
     const int i = mt * kTileRows + r;
-    float* row = out + b * bstride + (size_t)i * 2 * np + nt * CfgGJ::kBn + c0;
+    float4* row = reinterpret_cast<float4*>(out + b * bstride + (size_t)i * 2 * np + nt * CfgGJ::kBn + c0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      *reinterpret_cast<float4*>(row + 4 * u) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    for (int u = 0; u < 8; ++u) {
+      float4 x = row[u];
+      x.x += v[4 * u]; x.y += v[4 * u + 1]; x.z += v[4 * u + 2]; x.w += v[4 * u + 3];
+      row[u] = x;
+    }
   }
 };
 
@@ -2044,40 +2041,36 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
     p.rimg = rimg; p.r_batch = 2 * rs; p.r_slice = rs;
     p.c = c; p.m = m; p.eps = eps; p.q0 = q0; p.nb = nb; p.np = np; p.kt = 2 * np / kTileK; p.status = status;
     if (nb > kRedMaxBatch) return set_error(NEDMFT_EINVAL, "residual: batch %d > %d", nb, kRedMaxBatch);
-    // clusters of two CTAs sharing the A slices; as many clusters as fit at once
-    static int max_clusters = 0;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(64 + 32 * kOzEpiW);
-    cfg.dynamicSmemBytes = kOzSmem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (!max_clusters) {
-      NED_CUDA(cudaFuncSetAttribute(oz_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
-      cfg.gridDim = dim3(2);
-      NED_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, oz_residual_kernel, &cfg));
-      if (max_clusters < 1) return set_error(NEDMFT_ECUDA, "residual: no cluster of 2 fits on this device");
-    }
-    cfg.gridDim = dim3(2 * max_clusters);
-    NED_CUDA(cudaLaunchKernelEx(&cfg, oz_residual_kernel, p));
+    // one CTA per SM, persistent over the refined matrices' units
+    int sms = 0;
+    if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(oz_residual_kernel), kOzSmem))) return rc;
+    if ((rc = device_sm_count(&sms))) return rc;
+    oz_residual_kernel<<<sms, 64 + 32 * kOzEpiW, kOzSmem, st>>>(p);
     NED_LAUNCH_CHECK("oz_residual_kernel");
   }
-  {  // dX' = X' R' (bf16x3), refined points only
+  // dX' = X' R' + (X' R') R' (refined points only): the first two terms of
+  // X' (I - R')^-1 - X' = X' (R' + R'^2 + ...), both with the one residual R'.
+  // The first product in bf16x3; the second, |R'| times smaller, as one bf16
+  // product from the bf16 image of X' R' that the first one's epilogue writes
+  // (into the X' slice buffer, which the residual no longer needs).
+  {
     GemmParams p{aimg, 2 * as, as, rimg, 2 * rs, rs, 2 * np / kTileK, status};
-    EpiStore epi{reinterpret_cast<float*>(dx), 2 * mat, np};
-    static bool attr = false;
-    if (!attr) {
-      NED_CUDA(cudaFuncSetAttribute(umma_gemm_flag_kernel<CfgGJ, Split3, EpiStore>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, CfgGJ::kSmem));
-      attr = true;
-    }
+    EpiStore epi{reinterpret_cast<float*>(dx), 2 * mat, np, ximg, kOzS * xs};
+    if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(umma_gemm_flag_kernel<CfgGJ, Split3, EpiStore>),
+                              CfgGJ::kSmem)))
+      return rc;
     umma_gemm_flag_kernel<CfgGJ, Split3, EpiStore>
         <<<dim3(2 * np / CfgGJ::kBn, np / kTileRows, nb), 192, CfgGJ::kSmem, st>>>(p, epi, sh.flags, q0);
+    NED_LAUNCH_CHECK("umma_gemm_flag_kernel");
+  }
+  {
+    GemmParams p{ximg, kOzS * xs, 0, rimg, 2 * rs, rs, 2 * np / kTileK, status};
+    EpiAdd epi{reinterpret_cast<float*>(dx), 2 * mat, np};
+    if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(umma_gemm_flag_kernel<CfgHi, Split1, EpiAdd>),
+                              CfgHi::kSmem)))
+      return rc;
+    umma_gemm_flag_kernel<CfgHi, Split1, EpiAdd>
+        <<<dim3(2 * np / CfgHi::kBn, np / kTileRows, nb), 192, CfgHi::kSmem, st>>>(p, epi, sh.flags, q0);
     NED_LAUNCH_CHECK("umma_gemm_flag_kernel");
   }
   {
@@ -2095,6 +2088,34 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
       NED_LAUNCH_CHECK("reduce_refined_current_kernel");
     }
   }
+  return NEDMFT_OK;
+}
+
+namespace {
+// One CTA waits (bounded) on an mbarrier that nothing arrives at: the wait
+// runs out after the device's wait limit and records DS_TIMEOUT.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  abort_flag = 0;
+  fence_barrier_init();
+  if (!mbar_wait(&bar, 0, &abort_flag) && status) atomicCAS(status, 0, DS_TIMEOUT);
+}
+}  // namespace
+
+int umma_wait_selftest(int* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(status);
+  NED_LAUNCH_CHECK("wait_selftest_kernel");
+  return NEDMFT_OK;
+}
+
+// Limit of the bounded waits of this file's kernels on the current device
+// (stream-ordered after earlier work on `st`).
+int umma_set_wait_ns(uint64_t ns, cudaStream_t st) {
+  NED_CUDA(cudaMemcpyToSymbolAsync(umma::g_wait_ns, &ns, sizeof(ns), 0, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaStreamSynchronize(st));
   return NEDMFT_OK;
 }
 

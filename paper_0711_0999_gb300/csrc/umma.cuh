@@ -18,4 +18,10 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
                        const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
                        char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st);
 
+// Limit of the bounded device waits on the current device (synchronises st).
+int umma_set_wait_ns(uint64_t ns, cudaStream_t st);
+
+// A bounded wait on a barrier that nothing arrives at (records DS_TIMEOUT).
+int umma_wait_selftest(int* status, cudaStream_t st);
+
 }  // namespace nedmft

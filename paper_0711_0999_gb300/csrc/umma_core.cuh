@@ -70,16 +70,25 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for `parity` on `bar` for at most kWaitNs; on expiry set *abort and
-// return false.  Also returns false at once if another role aborted.
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+// Bounded waits.  A wait for work (a filled stage, a free stage, an
+// accumulator, a staging box) gives up after g_wait_ns nanoseconds of
+// %globaltimer (2 s unless nedmft_set_wait_limit changed it on this device),
+// sets *abort and returns false; it also returns false at once if another
+// role aborted.  The waits at exit for copies and products already issued
+// (so that no copy lands in, and no product reads, a CTA that has left, and
+// the TMEM is idle when released) use the fixed kDrainNs.
+// (This header belongs to one translation unit, which owns g_wait_ns.)
+constexpr uint64_t kDrainNs = 2000000000ull;  // 2 s
+constexpr uint64_t kWaitDefaultNs = 2000000000ull;
+static __device__ uint64_t g_wait_ns = kWaitDefaultNs;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
+  const uint64_t limit_ns = *reinterpret_cast<volatile uint64_t*>(&g_wait_ns);
   while (true) {
     if (mbar_test(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > kWaitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }
@@ -133,16 +142,6 @@ __device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, void* dst, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-// The same, multicast: the box lands at the same offset in the shared memory
-// of every CTA of the cluster in `mask`, each signalling its own `bar` (same offset).
-__device__ __forceinline__ void tma_load_4d_mc(const CUtensorMap* map, void* dst, int c0, int c1, int c2, int c3,
-                                               uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
 // Tiled 2D bulk store shared -> global through a tensor map.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
@@ -190,24 +189,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-// arrive on `bar` (same offset) in every CTA of the cluster in `mask` when
-// this thread's earlier MMAs complete
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// all threads of all CTAs of the cluster
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

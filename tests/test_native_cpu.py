@@ -79,12 +79,13 @@ def test_quadrature_grid_order():
 
 def test_workspace_sizes():
     g = api.contour_grid(-2, 4, 0.2, 10, 0.5)
-    for p in (N.FP64, N.MIXED_FP32, N.MIXED_BF16):
+    for p in (N.FP64, N.MIXED_BF16):
         assert api.lattice_workspace_size(g, 256, p) > 0
     big = api.contour_grid(-5, 30, 0.05, 10, 0.1)
     assert api.lattice_workspace_size(big, 2809, N.FP64) > api.lattice_workspace_size(g, 2809, N.FP64)
     assert N.lib().nedmft_lattice_workspace_size(ctypes.byref(g.contour), 0, 0, 0) == 0
     assert N.lib().nedmft_lattice_workspace_size(ctypes.byref(g.contour), 4, 7, 0) == 0
+    assert N.lib().nedmft_lattice_workspace_size(ctypes.byref(g.contour), 4, 2, 0) == 0  # no third precision
     assert N.lib().nedmft_impurity_workspace_size(ctypes.byref(g.contour)) > 0
     assert N.lib().nedmft_dmft_workspace_size(ctypes.byref(g.contour), 16, N.FP64) > 0
     assert N.lib().nedmft_dmft_workspace_size(ctypes.byref(g.contour), 0, N.FP64) == 0

@@ -73,3 +73,39 @@ def test_static_entry_rejects_large_contours():
                                             P(z), None, None, None)
     assert rc == N.NEDMFT_EINVAL
     assert b"static scratch limit" in N.lib().nedmft_last_error()
+
+
+def test_static_entry_matches_the_oracle_and_runs_gloc_only_on_a_side_stream():
+    # the result itself against the FP64 CPU oracle (1e-10 relative, the FP64
+    # contract), then the G_loc-only form (no current outputs) on a
+    # non-default stream against the workspace entry point on that stream
+    args = (-2, 3, 0.1, 4.0, 0.5)  # N_c = 108, close to the 112 limit
+    c = O.contour_grid(*args)
+    g = api.contour_grid(*args)
+    assert g.n_c == 108
+    mo, model = O.Model(U=1.0, E=2.0), api.make_model(1.0, 2.0)
+    sig = workload_sigma(c.t, c.w, 1.0, seed=3)
+    eps_h, ebar_h, wq_h = O.quadrature_points(6)
+    ref, jref = O.lattice_gloc(c, mo, sig, eps_h, ebar_h, wq_h)
+    sigma = torch.as_tensor(sig, device="cuda")
+    eps, ebar, wq = (torch.as_tensor(a, device="cuda") for a in (eps_h, ebar_h, wq_h))
+    gs, js, jis = _static_call(g, model, sigma, eps, ebar, wq)
+    scale = np.abs(ref).max()
+    assert np.abs(gs.cpu().numpy() - ref).max() < 1e-10 * scale
+    assert np.abs(js.cpu().numpy() - jref.real).max() < 1e-10
+    assert np.abs(jis.cpu().numpy() - jref.imag).max() < 1e-10
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    with torch.cuda.stream(side):
+        gloc = torch.empty_like(sigma)
+        rc = N.lib().nedmft_lattice_gloc_static(ctypes.byref(g.contour), ctypes.byref(model), P(sigma), P(eps),
+                                                P(ebar), P(wq), eps.numel(), P(gloc), None, None,
+                                                ctypes.c_void_p(side.cuda_stream))
+        N.check(rc)
+        gw, _, _ = api.lattice_gloc(g, model, sigma, eps, ebar, wq, precision="fp64", current=False, stream=side)
+    side.synchronize()
+    api.check_status(side)
+    assert (gloc - gw).abs().max().item() < 1e-12 * scale
+    assert np.abs(gloc.cpu().numpy() - ref).max() < 1e-10 * scale
