@@ -47,6 +47,8 @@ int* device_status_ptr();  // device address for the current device (cached)
 // only, so a process-wide "done" flag would skip them on a second GPU.
 int ensure_dyn_smem(const void* kern, int bytes);  // MaxDynamicSharedMemorySize >= bytes
 int device_sm_count(int* out);                     // multiprocessors of the current device
+// clusters of two CTAs of `kern` (block threads, dynamic shared bytes) that fit at once
+int max_active_clusters(const void* kern, int block, int smem_bytes, int* out);
 
 // ------------------------------------------------------------------ complex
 

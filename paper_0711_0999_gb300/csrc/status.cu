@@ -104,6 +104,40 @@ int ensure_dyn_smem(const void* kern, int bytes) {
   return NEDMFT_OK;
 }
 
+namespace {
+struct ClusterFit { const void* kern; int block, smem, clusters; };
+std::vector<ClusterFit> g_cluster_fit[kMaxDevices];
+}  // namespace
+
+int max_active_clusters(const void* kern, int block, int smem_bytes, int* out) {
+  int dev = 0;
+  NED_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(NEDMFT_ECUDA, "device %d beyond the library's table", dev);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const auto& f : g_cluster_fit[dev])
+    if (f.kern == kern && f.block == block && f.smem == smem_bytes) {
+      *out = f.clusters;
+      return NEDMFT_OK;
+    }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  NED_CUDA(cudaOccupancyMaxActiveClusters(&n, kern, &cfg));
+  if (n < 1) return set_error(NEDMFT_ECUDA, "no cluster of two CTAs with %d bytes of shared memory fits", smem_bytes);
+  g_cluster_fit[dev].push_back({kern, block, smem_bytes, n});
+  *out = n;
+  return NEDMFT_OK;
+}
+
 int device_sm_count(int* out) {
   int dev = 0;
   NED_CUDA(cudaGetDevice(&dev));

@@ -216,6 +216,13 @@ struct CfgHalf {
 };
 using CfgGJH = CfgHalf<256, 2, 2, 4>;
 
+// The same operands for a CTA pair, whose CTAs hold half of B each: the same
+// shared memory holds more, smaller stages (6 x 32 KB for 4 x 48 KB).
+template <class C>
+struct PairCfg : C {
+  static constexpr int kStages = (C::kStages * (C::kSa + C::kSb * C::kBTiles)) / (C::kSa + C::kSb);
+};
+
 // Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear
 // order (batch, m tile, n tile), n fastest, so that at any time the CTAs work
 // on about one matrix and its operand panels stay in L2.  The stage ring runs
@@ -243,25 +250,31 @@ struct PersistBars {
   int abort;
 };
 
-template <class C, class Pairs, class Epi, int EPIW>
+template <class C, class Pairs, class Epi, int EPIW, int PAIR>
 __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     umma_gemm_persistent_kernel(const __grid_constant__ TileMapParams p, const __grid_constant__ Epi epi, int n_tiles,
                                 int m_tiles, int batch) {
   static_assert(sizeof(PersistBars<C::kStages>) <= C::kBarBytes, "barrier block");
   static_assert(EPIW * kRedBuf <= kMaxBoxBars, "staging-box barriers");
+  static_assert(PAIR == 1 || (PAIR == 2 && C::kBTiles == 2), "a CTA pair splits B in halves of 128 rows");
+  // B half tiles per CTA and slice: a CTA of a pair holds half of B
+  constexpr int kBPer = PAIR == 2 ? 1 : C::kBTiles;
+  constexpr int kStageBytes = (C::kSa + C::kSb * kBPer) * C::kHalfBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  auto& bars = *reinterpret_cast<PersistBars<C::kStages>*>(smem + C::kStages * C::kStageBytes);
+  auto& bars = *reinterpret_cast<PersistBars<C::kStages>*>(smem + C::kStages * kStageBytes);
   uint64_t* full = bars.full;
   uint64_t* empty = bars.empty;
   uint64_t* acc_full = bars.acc_full;
   uint64_t* acc_empty = bars.acc_empty;
   volatile int* abort_flag = &bars.abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per_u = n_tiles * m_tiles;
+  // work units: (batch entry, m tile or pair of m tiles, n tile), n fastest
+  const int per_u = n_tiles * (m_tiles / PAIR);
   const int total = per_u * batch;
-  const int G = gridDim.x;
-  const int cta = blockIdx.x;
+  const int G = gridDim.x / PAIR;
+  const int cta = blockIdx.x / PAIR;
+  const int rank = PAIR == 2 ? (int)cluster_ctarank() : 0;
   constexpr uint32_t kCols = 2 * C::kBn;  // two accumulators
 
   if (threadIdx.x == 0) {
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], 32 * EPIW);
+      mbar_init(&acc_empty[s], PAIR * 32 * EPIW);  // a pair: the even CTA's barrier counts both CTAs
     }
     mbar_init(&bars.drain, 1);
     if (Epi::kStage)
@@ -279,9 +292,13 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(&bars.tmem_slot, kCols);
+  if (warp == 1) {
+    if constexpr (PAIR == 2) tmem_alloc_pair(&bars.tmem_slot, kCols);
+    else tmem_alloc(&bars.tmem_slot, kCols);
+  }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR == 2) cluster_sync();  // both CTAs' barriers exist before any remote arrival
   tc_fence_after();
   const uint32_t tmem = bars.tmem_slot;
 
@@ -291,34 +308,50 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       bool ok = true;
       for (int t = cta; t < total && ok; t += G) {
         const int b = t / per_u, rem = t % per_u;
-        const int mt = rem / n_tiles, nt = rem % n_tiles;
+        const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
         const long long a0 = p.a + b * p.a_batch + (long long)mt * p.kt;
         const long long b0 = p.b + b * p.b_batch + (long long)nt * C::kBTiles * p.kt;
         for (int h = 0; h < 2 * p.kt; ++h, ++it) {  // half tiles: kt = h / 2, core columns 4 (h % 2) .. +3
           const int s = it % C::kStages;
           const uint32_t ph = (it / C::kStages) & 1;
           if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) { ok = false; break; }
-          unsigned char* st = smem + s * C::kStageBytes;
+          unsigned char* st = smem + s * kStageBytes;
           const int kt = h >> 1, kc = 4 * (h & 1);
-          mbar_arrive_expect_tx(&full[s], C::kStageBytes);
-          for (int sa = 0; sa < C::kSa; ++sa)
-            tma_load_4d(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), &full[s]);
-          for (int sb = 0; sb < C::kSb; ++sb)
-            for (int u = 0; u < C::kBTiles; ++u)
-              tma_load_4d(&p.map, st + (C::kSa + sb * C::kBTiles + u) * C::kHalfBytes, 0, kc, 0,
-                          (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt), &full[s]);
+          if constexpr (PAIR == 2) {
+            // both CTAs' copies complete on the even CTA's barrier, which
+            // expects the bytes of both
+            const uint32_t fb = cluster_addr(&full[s], 0);
+            if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * kStageBytes);
+            for (int sa = 0; sa < C::kSa; ++sa)
+              tma_load_4d_pair(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), fb);
+            for (int sb = 0; sb < C::kSb; ++sb)
+              tma_load_4d_pair(&p.map, st + (C::kSa + sb) * C::kHalfBytes, 0, kc, 0,
+                               (int)(b0 + sb * p.b_slice + (long long)rank * p.kt + kt), fb);
+          } else {
+            mbar_arrive_expect_tx(&full[s], kStageBytes);
+            for (int sa = 0; sa < C::kSa; ++sa)
+              tma_load_4d(&p.map, st + sa * C::kHalfBytes, 0, kc, 0, (int)(a0 + sa * p.a_slice + kt), &full[s]);
+            for (int sb = 0; sb < C::kSb; ++sb)
+              for (int u = 0; u < C::kBTiles; ++u)
+                tma_load_4d(&p.map, st + (C::kSa + sb * C::kBTiles + u) * C::kHalfBytes, 0, kc, 0,
+                            (int)(b0 + sb * p.b_slice + (long long)u * p.kt + kt), &full[s]);
+          }
         }
       }
-      // no copy may be left in flight at exit
+      // no copy may be left in flight at exit: the even CTA (or a single one)
+      // waits for its stages to fill, the odd CTA of a pair, whose copies
+      // complete on the even CTA's barrier, for its stages to be released by
+      // the products (one bounded budget in all)
+      const uint64_t t0 = global_ns();
       for (int k = it - C::kStages < 0 ? 0 : it - C::kStages; k < it; ++k) {
-        const uint64_t t0 = global_ns();
-        while (!mbar_test(&full[k % C::kStages], (k / C::kStages) & 1) && global_ns() - t0 < kDrainNs) {
+        uint64_t* bar = (PAIR == 2 && rank == 1) ? &empty[k % C::kStages] : &full[k % C::kStages];
+        while (!mbar_test(bar, (k / C::kStages) & 1) && global_ns() - t0 < kDrainNs) {
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(128, C::kBn);
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128 * PAIR, C::kBn);
       int it = 0, lt = 0;
       bool ok = true;
       for (int t = cta; t < total && ok; t += G, ++lt) {
@@ -332,24 +365,44 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
           const int s = it % C::kStages;
           if (!mbar_wait(&full[s], (it / C::kStages) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+          const uint32_t st = smem_u32(smem + s * kStageBytes);
           // half tile: 4 core columns (LBO 128 B), 8-row groups 512 B apart
 #pragma unroll
           for (int kk = 0; kk < kTileK / 32; ++kk) {
 #pragma unroll
             for (int q = 0; q < Pairs::kPairs; ++q) {
               const uint32_t a_addr = st + Pairs::a(q) * C::kHalfBytes + kk * 256;
-              const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * C::kBTiles) * C::kHalfBytes + kk * 256;
-              mma_bf16(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc,
-                       (h > 0 || kk > 0 || q > 0) ? 1u : 0u);
+              const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * kBPer) * C::kHalfBytes + kk * 256;
+              const uint32_t acc = (h > 0 || kk > 0 || q > 0) ? 1u : 0u;
+              if constexpr (PAIR == 2)
+                mma_bf16_pair(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
+              else
+                mma_bf16(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
             }
           }
-          mma_commit(&empty[s]);
+          if constexpr (PAIR == 2) {
+            mma_commit_pair(cluster_addr(&empty[s], 0));
+            mma_commit_pair(cluster_addr(&empty[s], 1));
+          } else {
+            mma_commit(&empty[s]);
+          }
         }
-        if (ok) mma_commit(&acc_full[buf]);
+        if (ok) {
+          if constexpr (PAIR == 2) {
+            mma_commit_pair(cluster_addr(&acc_full[buf], 0));
+            mma_commit_pair(cluster_addr(&acc_full[buf], 1));
+          } else {
+            mma_commit(&acc_full[buf]);
+          }
+        }
       }
       // completes when every product issued above has (also after an abort)
-      mma_commit(&bars.drain);
+      if constexpr (PAIR == 2) {
+        mma_commit_pair(cluster_addr(&bars.drain, 0));
+        mma_commit_pair(cluster_addr(&bars.drain, 1));
+      } else {
+        mma_commit(&bars.drain);
+      }
     }
   } else {
     // EPIW epilogue warps: warp w owns TMEM lanes 32 (w % 4) .. +31 and one of
@@ -360,7 +413,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     constexpr int kSpan = C::kBn / kParts;
     // staging boxes start 1 KB after the barrier block (1024-byte aligned for
     // the swizzle); box k of this warp has the load barrier box_bar[k]
-    unsigned char* red_stage = smem + C::kStages * C::kStageBytes + 1024 + (warp - 2) * kRedBuf * kRedBox;
+    unsigned char* red_stage = smem + C::kStages * kStageBytes + 1024 + (warp - 2) * kRedBuf * kRedBox;
     uint64_t* box_bar = bars.box + (warp - 2) * kRedBuf;
     uint32_t box_phase = 0;    // bit k: parity of box_bar[k]'s next completion
     uint32_t box_loading = 0;  // bit k: a load into box k is in flight
@@ -369,7 +422,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     bool ok = true;
     for (int t = cta; t < total && ok; t += G, ++lt) {
       const int b = t / per_u, rem = t % per_u;
-      const int mt = rem / n_tiles, nt = rem % n_tiles;
+      const int mt = PAIR * (rem / n_tiles) + rank, nt = rem % n_tiles;
       const int buf = lt & 1;
       const int md = epi.mode(mt, nt);
       const int row = q * 32 + lane;
@@ -447,7 +500,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&acc_empty[buf]);
+      if constexpr (PAIR == 2) mbar_arrive_cluster(cluster_addr(&acc_empty[buf], 0));
+      else mbar_arrive(&acc_empty[buf]);
     }
     // no box load may be left in flight at exit (only after an abort)
     for (int k = 0; k < kRedBuf; ++k) {
@@ -464,8 +518,12 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     const uint64_t t0 = global_ns();
     while (!mbar_test(&bars.drain, 0) && global_ns() - t0 < kDrainNs) {
     }
+  }
+  if constexpr (PAIR == 2) cluster_sync();  // no remote arrival into, or product reading, a CTA that has left
+  if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, kCols);
+    if constexpr (PAIR == 2) tmem_dealloc_pair(tmem, kCols);
+    else tmem_dealloc(tmem, kCols);
   }
   if (threadIdx.x == 0 && *abort_flag && p.status) atomicCAS(p.status, 0, DS_TIMEOUT);
 }
@@ -473,9 +531,37 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
 template <class C, class Pairs, int EPIW, class Epi>
 int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi,
                            cudaStream_t st) {
-  const int smem_bytes = C::kSmem + (Epi::kStage ? red_stage_bytes<EPIW>() : 0);
   const dim3 block(64 + 32 * EPIW);
-  auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW>;
+  const int stage_extra = Epi::kStage ? red_stage_bytes<EPIW>() : 0;
+  if (m_tiles % 2 == 0 && C::kBTiles == 2) {
+    // CTA pairs: clusters of two, as many as fit at once
+    using CP = PairCfg<C>;
+    constexpr int kStagePair = (CP::kSa + CP::kSb) * CP::kHalfBytes;
+    const int smem_bytes = CP::kStages * kStagePair + 1024 + CP::kBarBytes + stage_extra;
+    auto kern = umma_gemm_persistent_kernel<CP, Pairs, Epi, EPIW, 2>;
+    int rc = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem_bytes);
+    int clusters = 0;
+    if (!rc) rc = max_active_clusters(reinterpret_cast<const void*>(kern), block.x, smem_bytes, &clusters);
+    if (rc) return rc;
+    const int units = n_tiles * (m_tiles / 2) * batch;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (units < clusters ? units : clusters));
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    NED_CUDA(cudaLaunchKernelEx(&cfg, kern, p, epi, n_tiles, m_tiles, batch));
+    NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
+    return NEDMFT_OK;
+  }
+  const int smem_bytes = C::kSmem + stage_extra;
+  auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 1>;
   int rc = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem_bytes);
   int sms = 0;
   if (!rc) rc = device_sm_count(&sms);
