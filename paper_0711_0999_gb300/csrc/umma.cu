@@ -213,14 +213,18 @@ struct CfgHalf {
   static constexpr int kStageBytes = (SA + SB * kBTiles) * kHalfBytes;
   static constexpr int kBarBytes = 512;
   static constexpr int kSmem = STAGES * kStageBytes + 1024 /*align*/ + kBarBytes;
+  static constexpr int kRedBuf = 2;  // staging boxes per epilogue warp
 };
 using CfgGJH = CfgHalf<256, 2, 2, 4>;
 
-// The same operands for a CTA pair, whose CTAs hold half of B each: the same
-// shared memory holds more, smaller stages (6 x 32 KB for 4 x 48 KB).
-template <class C>
+// The same operands for a CTA pair, whose CTAs hold half of B each: stages of
+// 32 KB instead of 48 KB.  The update (N_c = 1500) ran fastest with the freed
+// shared memory spent on stages (6 stages, 2 boxes: 1.41 ms per 152-matrix
+// launch; 5 and 3: 1.446; 4 and 6: 1.447; 4 and 4: 1.463).
+template <class C, int STAGES, int REDBUF>
 struct PairCfg : C {
-  static constexpr int kStages = (C::kStages * (C::kSa + C::kSb * C::kBTiles)) / (C::kSa + C::kSb);
+  static constexpr int kStages = STAGES;
+  static constexpr int kRedBuf = REDBUF;
 };
 
 // Persistent form: CTA c takes tiles c, c + G, c + 2G, ... of the linear
@@ -230,14 +234,14 @@ struct PairCfg : C {
 // tile overlaps the loads and products of the next.
 //
 // Epilogues with Epi::kStage stage -acc of plain tiles in shared memory, one
-// 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, kRedBuf
-// boxes per warp, and add it into the output at L2 with one tensor bulk
-// reduction per box through Epi::red_map.
-constexpr int kRedBuf = 2;
+// 32 x 32 FP32 box (4 KB, 128-byte swizzle) per warp and column chunk, C::kRedBuf
+// boxes per warp in a ring, and add it into the output at L2 with one tensor
+// bulk reduction per box through Epi::red_map.  Tiles whose old values the
+// epilogue needs load them into the same ring, C::kRedBuf chunks ahead.
 constexpr int kRedBox = 32 * 32 * 4;
-constexpr int kMaxBoxBars = 16;
-template <int EPIW>
-constexpr int red_stage_bytes() { return 512 + EPIW * kRedBuf * kRedBox; }
+constexpr int kMaxBoxBars = 32;
+template <class C, int EPIW>
+constexpr int red_stage_bytes() { return 512 + EPIW * C::kRedBuf * kRedBox; }
 
 // The barriers and flags of a persistent kernel, after its stage ring.
 template <int STAGES>
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
     umma_gemm_persistent_kernel(const __grid_constant__ TileMapParams p, const __grid_constant__ Epi epi, int n_tiles,
                                 int m_tiles, int batch) {
   static_assert(sizeof(PersistBars<C::kStages>) <= C::kBarBytes, "barrier block");
+  constexpr int kRedBuf = C::kRedBuf;
   static_assert(EPIW * kRedBuf <= kMaxBoxBars, "staging-box barriers");
   static_assert(PAIR == 1 || (PAIR == 2 && C::kBTiles == 2), "a CTA pair splits B in halves of 128 rows");
   // B half tiles per CTA and slice: a CTA of a pair holds half of B
@@ -427,8 +432,9 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
       const int md = epi.mode(mt, nt);
       const int row = q * 32 + lane;
       const int c_begin = part * kSpan, c_end = (part + 1) * kSpan;
-      // mode 2 tiles need the old values on the SM: chunk c's 32 x 32 box is
-      // loaded into box (c & 1) one chunk ahead, the first before the wait
+      // mode 2 tiles need the old values on the SM: chunk i's 32 x 32 box is
+      // loaded into box i % kRedBuf, kRedBuf chunks ahead, the first kRedBuf
+      // before the accumulator wait (so their latency hides behind the products)
       auto load_box = [&](int k, int c0) {
         if constexpr (Epi::kStage) {
           if (lane == 0) {
@@ -441,7 +447,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
         }
       };
       if constexpr (Epi::kStage) {
-        if (md == 2) load_box(0, c_begin);
+        if (md == 2)
+          for (int i = 0; i < kRedBuf && c_begin + 32 * i < c_end; ++i) load_box(i, c_begin + 32 * i);
       }
       // waits are made warp-uniform: the loop below issues .sync.aligned loads
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag))) break;
@@ -451,11 +458,11 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
         if constexpr (Epi::kStage) {
-          const int k = md == 2 ? ((c0 - c_begin) >> 5) & 1 : nred % kRedBuf;
+          const int ci = (c0 - c_begin) >> 5;  // chunk index within this warp's columns
+          const int k = md == 2 ? ci % kRedBuf : nred % kRedBuf;
           const bool keep = md == 2 && epi.keeps(mt, nt);
           unsigned char* box = red_stage + k * kRedBox;
           if (md == 2) {
-            if (c0 + 32 < c_end) load_box(k ^ 1, c0 + 32);
             if (!__all_sync(0xffffffffu, mbar_wait(&box_bar[k], (box_phase >> k) & 1, abort_flag))) {
               ok = false;
               break;
@@ -471,7 +478,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
 #pragma unroll
               for (int u = 0; u < 8; ++u)
                 *reinterpret_cast<float4*>(box + lane * 128 + ((u ^ (lane & 7)) << 4)) = o[u];
-            nred = k + 1;  // the next plain box is the other one
+            nred = k + 1;  // the next plain box follows in the ring
           } else {
             // -acc of the warp's 32 rows x 32 columns as one swizzled box
             // (row r, 16-byte chunk u at chunk u ^ (r & 7))
@@ -495,6 +502,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
               tma_store_2d(&epi.red_map, box, epi.red_x(nt, c0), epi.red_y(b, mt, q * 32));
             bulk_commit();
           }
+          // the box is free again (load_box first waits for the store to read it)
+          if (md == 2 && c0 + 32 * kRedBuf < c_end) load_box(k, c0 + 32 * kRedBuf);
         } else {
           epi(b, mt, nt, row, c0, v);
         }
@@ -532,12 +541,12 @@ template <class C, class Pairs, int EPIW, class Epi>
 int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int batch, const Epi& epi,
                            cudaStream_t st) {
   const dim3 block(64 + 32 * EPIW);
-  const int stage_extra = Epi::kStage ? red_stage_bytes<EPIW>() : 0;
+  const int stage_extra_single = Epi::kStage ? red_stage_bytes<C, EPIW>() : 0;
   if (m_tiles % 2 == 0 && C::kBTiles == 2) {
     // CTA pairs: clusters of two, as many as fit at once
-    using CP = PairCfg<C>;
+    using CP = PairCfg<C, 6, 2>;
     constexpr int kStagePair = (CP::kSa + CP::kSb) * CP::kHalfBytes;
-    const int smem_bytes = CP::kStages * kStagePair + 1024 + CP::kBarBytes + stage_extra;
+    const int smem_bytes = CP::kStages * kStagePair + 1024 + CP::kBarBytes + (Epi::kStage ? red_stage_bytes<CP, EPIW>() : 0);
     auto kern = umma_gemm_persistent_kernel<CP, Pairs, Epi, EPIW, 2>;
     int rc = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem_bytes);
     int clusters = 0;
@@ -560,7 +569,7 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
     NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
     return NEDMFT_OK;
   }
-  const int smem_bytes = C::kSmem + stage_extra;
+  const int smem_bytes = C::kSmem + stage_extra_single;
   auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 1>;
   int rc = ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem_bytes);
   int sms = 0;
