@@ -37,7 +37,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="production N_c=1500 (U=1, E=1, beta=10, t in [-5,30], dt=0.05, dtau=0.1, 53x53 points)",
                 t_min=-5.0, t_max=30.0, dt=0.05, beta=10.0, dtau=0.1, U=1.0, E=1.0, n_quad=53)
 # the warm-start configuration: training runs on a shorter contour, evaluation on the production one
-WARM_TRAIN = dict(contour=(-5.0, 10.0, 0.1, 10.0, 0.1), n_quad=32, U=(0.25, 2.5), E=(0.25, 4.0), seed=20071101)
+# (the network learns the discrete impurity Green's function at two steps, dt = 0.1 and 0.2, and the warm
+# start extrapolates in dt to the production step 0.05)
+WARM_TRAIN = dict(contours=((-5.0, 10.0, 0.1, 10.0, 0.1), (-5.0, 10.0, 0.2, 10.0, 0.1)), n_quad=32,
+                  U=(0.25, 2.5), E=(0.25, 4.0), seed=20071101)
 TTS_TOL = 1e-6  # the paper's pointwise convergence criterion (one part in 10^6)
 METRIC = "DMFT iterations/s & TFLOP/s at N_c≈1500; mixed+warm-start vs FP64 at 1e-6 err"
 DTYPES = {"fp64": "f64", "mixed_bf16": "bf16x3+f64"}
@@ -312,8 +315,8 @@ def warm_start_network(n_runs: int, log=None):
     rng = np.random.default_rng(WARM_TRAIN["seed"])
     runs = list(zip(rng.uniform(*WARM_TRAIN["U"], n_runs), rng.uniform(*WARM_TRAIN["E"], n_runs)))
     t0 = time.perf_counter()
-    x, t, its = warmstart.collect(runs, WARM_TRAIN["contour"], WARM_TRAIN["n_quad"], "mixed_bf16", tol=1e-7,
-                                  max_iter=150)
+    x, t, its, conv = warmstart.collect(runs, WARM_TRAIN["contours"], WARM_TRAIN["n_quad"], "mixed_bf16", tol=1e-7,
+                                        max_iter=150)
     torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -321,7 +324,9 @@ def warm_start_network(n_runs: int, log=None):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     losses = losses.cpu().numpy()
-    return params, {"runs": n_runs, "n_c": 400, "points": WARM_TRAIN["n_quad"] ** 2, "collect_s": t_collect,
+    return params, {"runs": n_runs, "solves": len(conv), "solves_converged": int(sum(conv)), "n_c": [400, 250],
+                    "dt": [0.1, 0.2],
+                    "points": WARM_TRAIN["n_quad"] ** 2, "collect_s": t_collect,
                     "train_s": t_train, "loss_start": float(losses[:20].mean()),
                     "loss_end": float(losses[-100:].mean()), "iterations_per_run": its}
 
@@ -366,7 +371,7 @@ def time_to_solution(n_train: int, n_eval: int, with_fp64: bool = True):
         row = {"U": float(U), "E": float(E), "iters_zero": zero.iterations, "s_zero": t_zero,
                "iters_band": band.iterations, "s_band": t_band, "converged": bool(zero.converged)}
         if params is not None:
-            warm, t_warm = solve(m, lambda: warmstart.warm_start(g, m, params))
+            warm, t_warm = solve(m, lambda: warmstart.initial_sigma(g, m, params))
             row.update({"iters_warm": warm.iterations, "s_warm": t_warm, "converged": bool(row["converged"] and
                                                                                             warm.converged),
                         "gloc_rel_diff_warm_vs_zero": float((warm.gloc - zero.gloc).abs().max() /

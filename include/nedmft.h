@@ -347,24 +347,32 @@ int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
 
 /* ---------------------------------------------------------------- learned warm start */
 
-/* A multilayer perceptron that predicts the smooth part of Sigma(t, t') from
- * (U, E, t, t') -- a starting guess for the DMFT loop in place of the
- * equilibrium self-energy the paper starts from (Sec. II, the summary of the
- * iterative algorithm).  The result of the loop does not depend on the guess;
- * only the number of iterations does.
- * Network: 14 features -> 4 tanh layers of 256 -> 2 outputs (Re, Im).
+/* A multilayer perceptron whose prediction starts the DMFT loop in place of
+ * the equilibrium self-energy the paper starts from (Sec. II, the summary of
+ * the iterative algorithm).  The result of the loop does not depend on the
+ * guess; only the number of iterations does.
+ * What it predicts: the impurity Green's function X = inv(A0 + (1 - w1) D)
+ * of the impurity step (nedmft_impurity_update), from which the self-energy
+ * follows exactly: W Sigma W = -w1 D + w1 (1 - w1) D X D.  X is smooth along
+ * the contour and of order one for any U; Sigma itself carries ratios of the
+ * step sizes in the columns at the ends of the branches, which no network that
+ * does not know the grid could predict.
+ * Network: 17 features -> 4 tanh layers of 256 -> 2 outputs (Re, Im of X).
  * Parameters: one FP32 array of nedmft_mlp_param_count() values, layer by
  * layer, each layer a row-major (in x out) weight block followed by its
  * out biases.  GEMM operands are rounded to bf16, sums are FP32.
- * Features of the pair (t_i, t_j): U/2.5, E/4, Re(t_i - t_j)/20,
- * (tau_i - tau_j)/beta, then for t_i and t_j in turn Re t / 20, tau / beta,
- * one-hot branch (upper, lower, imaginary).
- * Targets: (Sigma - U w1 delta_c) / scale, the point-split band removed
- * (delta_c(t_j, t_{j-1}) = 1/W_{j-1}, boundary element -1/W_{N-1}). */
+ * Features of the pair (t_a, t_b), chosen to carry over from short training
+ * contours to longer ones: U/2.5, E/4, tanh(Re(t_a - t_b)/3), then for t_a
+ * and t_b in turn (real part r, imaginary depth tau) tanh(max(r, 0)/3) (the
+ * elapsed field time, saturating), min(r, 0)/5, tau/beta and the one-hot
+ * branch (upper, lower, imaginary); then the contour order (1 for a >= b) and
+ * dt / 0.1 (the discrete X differs from the continuum one at order dt).
+ * Targets: X[a][b] = [W Sigma W + w1 D]_{a+1, b-1} / (w1 (1 - w1) d_{a+1} d_b)
+ * / scale (indices mod N; d_i = -U W_i for i >= 1, d_0 = +U W_0). */
 int32_t nedmft_mlp_param_count(void);
 /* Workspace bytes for n samples of nedmft_mlp_forward / nedmft_mlp_grad. */
 size_t nedmft_mlp_workspace_size(int32_t n);
-/* y_d (n x 2) = network(x_d (n x 14)).  Device arrays. */
+/* y_d (n x 2) = network(x_d (n x 17)).  Device arrays. */
 int nedmft_mlp_forward(const float* params_d, const float* x_d, int32_t n,
                        float* y_d, void* ws_d, size_t ws_bytes, void* stream);
 /* Mean-squared error over the n x 2 outputs against target_d and its
@@ -376,7 +384,7 @@ int nedmft_mlp_grad(const float* params_d, const float* x_d,
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step number step >= 1. */
 int nedmft_mlp_adam(float* params_d, const float* grad_d, float* m1_d,
                     float* m2_d, int32_t step, float lr, void* stream);
-/* Features of every (t_i, t_j) pair of the contour: x_d is n_c^2 x 14. */
+/* Features of every (t_a, t_b) pair of the contour (dt feature c->dt): x_d is n_c^2 x 17. */
 int nedmft_mlp_features(const nedmft_contour* c, const nedmft_model* m,
                         float* x_d, void* stream);
 /* Targets of every pair from a self-energy: t_d is n_c^2 x 2. */
@@ -384,18 +392,22 @@ int nedmft_mlp_target(const nedmft_contour* c, const nedmft_model* m,
                       const nedmft_c128* sigma_d, double scale, float* t_d,
                       void* stream);
 /* A random minibatch (a counter-based hash of seed, step and row picks each
- * sample) of batch rows from n_total samples: xb_d batch x 14, tb_d batch x 2. */
+ * sample) of batch rows from n_total samples: xb_d batch x 17, tb_d batch x 2. */
 int nedmft_mlp_sample(const float* x_d, const float* t_d, int64_t n_total,
                       int32_t batch, uint64_t seed, int64_t step, float* xb_d,
                       float* tb_d, void* stream);
 /* Workspace bytes for nedmft_sigma_warm_start on this contour. */
 size_t nedmft_sigma_warm_start_workspace_size(const nedmft_contour* c);
-/* sigma_d = U w1 delta_c + scale * network(features): the warm start for
- * nedmft_dmft_solve's sigma_init_d. */
+/* The warm start for nedmft_dmft_solve's sigma_init_d on contour c: the
+ * network's X on this contour's times with the dt feature set to each of the
+ * n_dt training steps dts_host[k] (1 <= n_dt <= 8, distinct, > 0), combined
+ * by Lagrange extrapolation to c->dt (the paper's dt -> 0 extrapolation, here
+ * to the contour's own step), then sigma_d = W^-1 (-w1 D + w1 (1 - w1) D X D)
+ * W^-1.  Needs U != 0 and 0 < w1 < 1.  Stream-ordered. */
 int nedmft_sigma_warm_start(const nedmft_contour* c, const nedmft_model* m,
-                            const float* params_d, double scale,
-                            nedmft_c128* sigma_d, void* ws_d, size_t ws_bytes,
-                            void* stream);
+                            const float* params_d, int32_t n_dt,
+                            const double* dts_host, nedmft_c128* sigma_d,
+                            void* ws_d, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- loop */
 

@@ -3,17 +3,19 @@
 TEST INFRASTRUCTURE ONLY (imported by tests/ alone).  The network is not part
 of the paper's method: it only supplies a starting self-energy, and the DMFT
 loop's converged result does not depend on it.  This module restates, in
-NumPy, the layer layout, features, targets, forward pass, mean-squared-error
-gradient and the bf16 rounding of GEMM operands that the CUDA kernels use, so
-their gradients can be checked; its FP64 unrounded gradient is pinned by
-finite differences in tests/test_mlp_pins.py.
+NumPy, the layer layout, features, the map between the self-energy and the
+impurity Green's function X the network learns (W Sigma W = -w1 D +
+w1 (1 - w1) D X D, the impurity step's identity), forward pass,
+mean-squared-error gradient and the bf16 rounding of GEMM operands that the
+CUDA kernels use, so their gradients can be checked; its FP64 unrounded
+gradient is pinned by finite differences in tests/test_mlp_pins.py.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-DIMS = [14, 256, 256, 256, 256, 2]
+DIMS = [17, 256, 256, 256, 256, 2]
 
 
 def param_count() -> int:
@@ -81,23 +83,52 @@ def loss_and_grad(params, x, t, rounded=True):
     return loss, np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
 
 
-def features(c, U: float, E: float) -> np.ndarray:
-    """Per pair (t_i, t_j): U/2.5, E/4, Re(t_i - t_j)/20, (tau_i - tau_j)/beta, then for
-    each time Re t / 20, tau / beta, branch one-hot."""
+def features(c, U: float, E: float, dt_feature: float | None = None) -> np.ndarray:
+    """Per pair (t_a, t_b): U/2.5, E/4, tanh(Re(t_a - t_b)/3), then for each time
+    (real part r, imaginary depth tau) tanh(max(r, 0)/3), min(r, 0)/5, tau/beta and
+    the branch one-hot, then the contour order (1 for a >= b) and dt/0.1 (the
+    contour's own step unless dt_feature is given)."""
     n = c.n_c
-    per = np.zeros((n, 5))
+    r = c.t.real
+    per = np.zeros((n, 6))
     for k in range(n):
-        per[k, 0] = c.t[k].real / 20.0
-        per[k, 1] = -c.t[k].imag / c.beta
-        per[k, 2 + (0 if k < c.n_t else (1 if k < 2 * c.n_t else 2))] = 1.0
-    f = np.zeros((n, n, 14))
+        per[k, 0] = np.tanh(max(r[k], 0.0) / 3.0)
+        per[k, 1] = min(r[k], 0.0) / 5.0
+        per[k, 2] = -c.t[k].imag / c.beta
+        per[k, 3 + (0 if k < c.n_t else (1 if k < 2 * c.n_t else 2))] = 1.0
+    f = np.zeros((n, n, 17))
     f[:, :, 0] = U / 2.5
     f[:, :, 1] = E / 4.0
-    f[:, :, 2] = per[:, None, 0] - per[None, :, 0]
-    f[:, :, 3] = per[:, None, 1] - per[None, :, 1]
-    f[:, :, 4:9] = per[:, None, :]
-    f[:, :, 9:14] = per[None, :, :]
-    return f.reshape(n * n, 14)
+    f[:, :, 2] = np.tanh((r[:, None] - r[None, :]) / 3.0)
+    f[:, :, 3:9] = per[:, None, :]
+    f[:, :, 9:15] = per[None, :, :]
+    f[:, :, 15] = np.tril(np.ones((n, n)))
+    f[:, :, 16] = (c.dt if dt_feature is None else dt_feature) / 0.1
+    return f.reshape(n * n, 17)
+
+
+def d_matrix(c, U: float) -> np.ndarray:
+    """D = i [M(mu - U) - M(mu)]: -U W_i at (i, i-1) for i >= 1, +U W_0 at (0, N-1)."""
+    n = c.n_c
+    D = np.zeros((n, n), complex)
+    for i in range(1, n):
+        D[i, i - 1] = -U * c.w[i]
+    D[0, n - 1] = U * c.w[0]
+    return D
+
+
+def sigma_from_xh(c, X: np.ndarray, U: float, w1: float) -> np.ndarray:
+    """Sigma from X by W Sigma W = -w1 D + w1 (1 - w1) D X D."""
+    D = d_matrix(c, U)
+    return (-w1 * D + w1 * (1 - w1) * D @ X @ D) / (c.w[:, None] * c.w[None, :])
+
+
+def xh_from_sigma(c, sigma: np.ndarray, U: float, w1: float) -> np.ndarray:
+    """X from Sigma, the inverse of sigma_from_xh (D is invertible for U != 0)."""
+    D = d_matrix(c, U)
+    Di = np.linalg.inv(D)
+    S = c.w[:, None] * sigma * c.w[None, :]
+    return Di @ (S + w1 * D) @ Di / (w1 * (1 - w1))
 
 
 def band(c, U: float, w1: float) -> np.ndarray:

@@ -92,7 +92,7 @@ SIGNATURES = {
     "nedmft_mlp_sample": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int64, c_int32, ctypes.c_uint64, ctypes.c_int64,
                                          c_void_p, c_void_p, c_void_p]),
     "nedmft_sigma_warm_start_workspace_size": (c_size_t, [PC]),
-    "nedmft_sigma_warm_start": (ctypes.c_int, [PC, PM, c_void_p, c_double, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nedmft_sigma_warm_start": (ctypes.c_int, [PC, PM, c_void_p, c_int32, PD, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nedmft_lattice_autotune": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_int,
                                                PI, c_int32, PI, PD, c_void_p, c_size_t, c_void_p]),
     "nedmft_lattice_batch": (c_int32, [PC, c_int32, ctypes.c_int]),

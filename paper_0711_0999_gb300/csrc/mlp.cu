@@ -1,6 +1,12 @@
-// Learned warm start of the self-energy: a small MLP maps (U, E, t, t') to
-// the smooth part of Sigma(t, t'); the point-split band U<w_1> delta_c is
-// added in closed form.  Forward, backward (mean-squared error) and Adam are
+// Learned warm start of the self-energy.  The impurity step gives
+//   W Sigma W = -w1 D + w1 (1 - w1) D X D,  X = inv(A0 + (1 - w1) D),
+// with D the point-split difference of the M matrices (one entry per row:
+// d_i at (i, i-1), indices mod N, d_i = -U W_i for i >= 1, d_0 = +U W_0).  X
+// is an impurity Green's function -- smooth along the contour, of order one
+// for any U, with its jump at equal contour times -- while Sigma itself carries
+// factors of the step sizes at the ends of the branches.  A small MLP maps
+// (U, E, dt, t, t') to X(t, t'); the self-energy follows from the identity
+// above.  Forward, backward (mean-squared error) and Adam are
 // hand-written kernels; GEMM operands are rounded to bf16 and accumulated in
 // FP32, weights and optimizer state are FP32.
 #include <math.h>
@@ -10,7 +16,7 @@
 namespace nedmft {
 namespace {
 
-constexpr int kIn = 14;      // features per (t, t') pair
+constexpr int kIn = 17;      // features per (t, t') pair
 constexpr int kHid = 256;    // width of the four hidden layers
 constexpr int kOut = 2;      // Re, Im of the smooth Sigma part
 constexpr int kLayers = 5;   // 4 hidden + output
@@ -147,79 +153,93 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
-// Features of the pair (t_i, t_j): U/2.5, E/4, Re(t_i - t_j)/20,
-// (tau_i - tau_j)/beta, then for each time Re t / 20, tau / beta and the
-// branch one-hot (upper, lower, imaginary).
-__global__ void features_kernel(ContourDev c, ModelDev m, float* __restrict__ x) {
+// Features of the pair (t_a, t_b) of X, built to carry over to contours
+// longer than the training runs' (the field is switched on at t = 0; after a
+// few units of time a metal's Green's function depends on t - t' alone):
+// U/2.5, E/4, tanh(Re(t_a - t_b)/3), then for each time t (real part r,
+// imaginary-branch depth tau) tanh(max(r, 0)/3) (the elapsed field time,
+// saturating), min(r, 0)/5 (the time before the field), tau/beta and the
+// branch one-hot (upper, lower, imaginary), then the contour order
+// theta_c(t_a, t_b) (1 for a >= b), across which X jumps, and dt / 0.1 (the
+// discrete X differs from the continuum one at order dt, so the network learns
+// it at the training steps and the warm start extrapolates in dt).
+__global__ void features_kernel(ContourDev c, ModelDev m, double dt_feature, float* __restrict__ x) {
   const size_t total = (size_t)c.n * c.n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / c.n), j = (int)(e % c.n);
     float* f = x + e * kIn;
     f[0] = (float)(m.U / 2.5);
     f[1] = (float)(m.E / 4.0);
-    f[2] = (float)((t_re(c, i) - t_re(c, j)) / 20.0);
-    f[3] = (float)((t_tau(c, i) - t_tau(c, j)) / c.beta);
+    f[2] = (float)tanh((t_re(c, i) - t_re(c, j)) / 3.0);
     const int ij[2] = {i, j};
     for (int s = 0; s < 2; ++s) {
       const int k = ij[s];
-      f[4 + 5 * s] = (float)(t_re(c, k) / 20.0);
-      f[5 + 5 * s] = (float)(t_tau(c, k) / c.beta);
-      f[6 + 5 * s] = k < c.nt ? 1.f : 0.f;
-      f[7 + 5 * s] = (k >= c.nt && k < 2 * c.nt) ? 1.f : 0.f;
-      f[8 + 5 * s] = k >= 2 * c.nt ? 1.f : 0.f;
+      const double r = t_re(c, k);
+      f[3 + 6 * s] = (float)tanh(fmax(r, 0.0) / 3.0);
+      f[4 + 6 * s] = (float)(fmin(r, 0.0) / 5.0);
+      f[5 + 6 * s] = (float)(t_tau(c, k) / c.beta);
+      f[6 + 6 * s] = k < c.nt ? 1.f : 0.f;
+      f[7 + 6 * s] = (k >= c.nt && k < 2 * c.nt) ? 1.f : 0.f;
+      f[8 + 6 * s] = k >= 2 * c.nt ? 1.f : 0.f;
     }
+    f[15] = i >= j ? 1.f : 0.f;
+    f[16] = (float)(dt_feature / 0.1);
   }
 }
 
-// Sigma = band + scale * y: the point-split band (U w1) delta_c
-// (Sigma_{j,j-1} = U w1 / W_{j-1}, boundary element -U w1 / W_{N-1}) plus the
-// network's smooth part.
-__global__ void assemble_sigma_kernel(ContourDev c, ModelDev m, const float* __restrict__ y, double scale,
+// d_i, the entry of D in row i (column i - 1 mod N).
+__device__ __forceinline__ double2 d_entry(const ContourDev& c, double U, int i) {
+  const double2 w = weight(c, i);
+  return i == 0 ? make_double2(U * w.x, U * w.y) : make_double2(-U * w.x, -U * w.y);
+}
+
+// Sigma from X: W Sigma W = -w1 D + w1 (1 - w1) D X D, i.e.
+// Sigma_ij = [-w1 D_ij + w1 (1 - w1) d_i X[i-1][j+1] d_{j+1}] / (W_i W_j)
+// (indices mod N); X[a][b] is the complex value y[(a N + b)] (Re, Im).
+__global__ void assemble_sigma_kernel(ContourDev c, ModelDev m, const float* __restrict__ y,
                                       double2* __restrict__ sigma) {
-  const size_t total = (size_t)c.n * c.n;
+  const int n = c.n;
+  const size_t total = (size_t)n * n;
+  const double w1 = m.w1;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / c.n), j = (int)(e % c.n);
-    double2 v = make_double2(scale * y[2 * e], scale * y[2 * e + 1]);
-    const double h = m.U * m.w1;
-    if (j == i - 1) {
-      const double2 w = weight(c, j);
-      const double d = w.x * w.x + w.y * w.y;
-      v.x += h * w.x / d;
-      v.y -= h * w.y / d;
-    }
-    if (i == 0 && j == c.n - 1) {
-      const double2 w = weight(c, c.n - 1);
-      const double d = w.x * w.x + w.y * w.y;
-      v.x -= h * w.x / d;
-      v.y += h * w.y / d;
-    }
-    sigma[e] = v;
+    const int i = (int)(e / n), j = (int)(e % n);
+    const int ip = i == 0 ? n - 1 : i - 1, jn = j + 1 == n ? 0 : j + 1;
+    const size_t f = (size_t)ip * n + jn;
+    const double2 x = make_double2(y[2 * f], y[2 * f + 1]);
+    const double2 di = d_entry(c, m.U, i);
+    double2 v = cmul(cmul(di, x), d_entry(c, m.U, jn));
+    v = make_double2(w1 * (1.0 - w1) * v.x, w1 * (1.0 - w1) * v.y);
+    if (j == ip) v = make_double2(v.x - w1 * di.x, v.y - w1 * di.y);
+    const double2 ww = cmul(weight(c, i), weight(c, j));
+    const double m2 = ww.x * ww.x + ww.y * ww.y;
+    sigma[e] = cmul(v, make_double2(ww.x / m2, -ww.y / m2));
   }
 }
 
-// The training target: the smooth part (Sigma minus the band) / scale.
+// The training target X[a][b] = [W Sigma W + w1 D]_{a+1, b-1} / (w1 (1 - w1) d_{a+1} d_b), / scale.
 __global__ void target_kernel(ContourDev c, ModelDev m, const double2* __restrict__ sigma, double inv_scale,
                               float* __restrict__ t) {
-  const size_t total = (size_t)c.n * c.n;
+  const int n = c.n;
+  const size_t total = (size_t)n * n;
+  const double w1 = m.w1;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / c.n), j = (int)(e % c.n);
-    double2 v = sigma[e];
-    const double h = m.U * m.w1;
-    if (j == i - 1) {
-      const double2 w = weight(c, j);
-      const double d = w.x * w.x + w.y * w.y;
-      v.x -= h * w.x / d;
-      v.y += h * w.y / d;
-    }
-    if (i == 0 && j == c.n - 1) {
-      const double2 w = weight(c, c.n - 1);
-      const double d = w.x * w.x + w.y * w.y;
-      v.x += h * w.x / d;
-      v.y -= h * w.y / d;
-    }
+    const int a = (int)(e / n), b = (int)(e % n);
+    const int i = a + 1 == n ? 0 : a + 1, j = b == 0 ? n - 1 : b - 1;
+    const double2 di = d_entry(c, m.U, i);
+    double2 v = cmul(cmul(weight(c, i), sigma[(size_t)i * n + j]), weight(c, j));
+    if (j == (i == 0 ? n - 1 : i - 1)) v = make_double2(v.x + w1 * di.x, v.y + w1 * di.y);
+    const double2 den = cmul(di, d_entry(c, m.U, b));
+    const double dm = w1 * (1.0 - w1) * (den.x * den.x + den.y * den.y);
+    v = cmul(v, make_double2(den.x / dm, -den.y / dm));
     t[2 * e] = (float)(v.x * inv_scale);
     t[2 * e + 1] = (float)(v.y * inv_scale);
   }
+}
+
+// y <- y + lk * yk (n2 complex pairs of FP32): one term of the dt extrapolation.
+__global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ yk, float lk, size_t n, bool first) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = (first ? 0.f : y[e]) + lk * yk[e];
 }
 
 int grid_for(size_t n) {
@@ -336,7 +356,7 @@ extern "C" int nedmft_mlp_features(const nedmft_contour* c, const nedmft_model* 
   if (!c || !m || !x_d || c->n_c < 1) return set_error(NEDMFT_EINVAL, "mlp_features: bad argument");
   const ContourDev cd = to_dev(*c);
   const ModelDev md{m->U, m->E, m->w1, isnan(m->mu) ? m->U / 2 : m->mu};
-  features_kernel<<<grid_for((size_t)cd.n * cd.n), 256, 0, static_cast<cudaStream_t>(stream)>>>(cd, md, x_d);
+  features_kernel<<<grid_for((size_t)cd.n * cd.n), 256, 0, static_cast<cudaStream_t>(stream)>>>(cd, md, cd.dt, x_d);
   NED_LAUNCH_CHECK("features_kernel");
   return NEDMFT_OK;
 }
@@ -355,14 +375,21 @@ extern "C" int nedmft_mlp_target(const nedmft_contour* c, const nedmft_model* m,
 extern "C" size_t nedmft_sigma_warm_start_workspace_size(const nedmft_contour* c) {
   if (!c || c->n_c < 1) return 0;
   const size_t n2 = (size_t)c->n_c * c->n_c;
-  return align256(sizeof(float) * n2 * kIn) + align256(sizeof(float) * n2 * kOut) +
+  return align256(sizeof(float) * n2 * kIn) + 2 * align256(sizeof(float) * n2 * kOut) +
          nedmft_mlp_workspace_size((int32_t)(n2 > 65536 ? 65536 : n2));
 }
 
 extern "C" int nedmft_sigma_warm_start(const nedmft_contour* c, const nedmft_model* m, const float* params_d,
-                                       double scale, nedmft_c128* sigma_d, void* ws_d, size_t ws_bytes, void* stream) {
-  if (!c || !m || !params_d || !sigma_d || !ws_d || !(scale > 0))
+                                       int32_t n_dt, const double* dts_host, nedmft_c128* sigma_d, void* ws_d,
+                                       size_t ws_bytes, void* stream) {
+  if (!c || !m || !params_d || !sigma_d || !ws_d || !dts_host || n_dt < 1 || n_dt > 8)
     return set_error(NEDMFT_EINVAL, "sigma_warm_start: bad argument");
+  if (!(m->U != 0.0) || !(m->w1 > 0.0 && m->w1 < 1.0))
+    return set_error(NEDMFT_EINVAL, "sigma_warm_start: needs U != 0 and 0 < w1 < 1");
+  for (int k = 0; k < n_dt; ++k)
+    for (int q = 0; q < k; ++q)
+      if (!(dts_host[k] > 0.0) || dts_host[k] == dts_host[q])
+        return set_error(NEDMFT_EINVAL, "sigma_warm_start: steps must be positive and distinct");
   if (ws_bytes < nedmft_sigma_warm_start_workspace_size(c))
     return set_error(NEDMFT_ENOMEM, "sigma_warm_start: workspace too small");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -370,17 +397,28 @@ extern "C" int nedmft_sigma_warm_start(const nedmft_contour* c, const nedmft_mod
   char* p = static_cast<char*>(ws_d);
   float* x = reinterpret_cast<float*>(p);
   float* y = reinterpret_cast<float*>(p + align256(sizeof(float) * n2 * kIn));
-  char* mws = p + align256(sizeof(float) * n2 * kIn) + align256(sizeof(float) * n2 * kOut);
-  int rc = nedmft_mlp_features(c, m, x, stream);
-  if (rc) return rc;
-  for (size_t s = 0; s < n2; s += 65536) {  // evaluate in chunks of 65536 pairs
-    const int cnt = (int)((n2 - s) < 65536 ? (n2 - s) : 65536);
-    rc = nedmft_mlp_forward(params_d, x + s * kIn, cnt, y + s * kOut, mws, nedmft_mlp_workspace_size(cnt), stream);
-    if (rc) return rc;
-  }
+  float* yk = reinterpret_cast<float*>(p + align256(sizeof(float) * n2 * kIn) + align256(sizeof(float) * n2 * kOut));
+  char* mws = p + align256(sizeof(float) * n2 * kIn) + 2 * align256(sizeof(float) * n2 * kOut);
   const ContourDev cd = to_dev(*c);
   const ModelDev md{m->U, m->E, m->w1, isnan(m->mu) ? m->U / 2 : m->mu};
-  assemble_sigma_kernel<<<grid_for(n2), 256, 0, st>>>(cd, md, y, scale, reinterpret_cast<double2*>(sigma_d));
+  for (int k = 0; k < n_dt; ++k) {
+    // X at the step dts[k] on this contour's times, weighted by the Lagrange
+    // basis polynomial of dts[k] at this contour's step (extrapolation in dt)
+    double lk = 1.0;
+    for (int q = 0; q < n_dt; ++q)
+      if (q != k) lk *= (cd.dt - dts_host[q]) / (dts_host[k] - dts_host[q]);
+    features_kernel<<<grid_for(n2), 256, 0, st>>>(cd, md, dts_host[k], x);
+    NED_LAUNCH_CHECK("features_kernel");
+    for (size_t s = 0; s < n2; s += 65536) {  // evaluate in chunks of 65536 pairs
+      const int cnt = (int)((n2 - s) < 65536 ? (n2 - s) : 65536);
+      int rc = nedmft_mlp_forward(params_d, x + s * kIn, cnt, yk + s * kOut, mws, nedmft_mlp_workspace_size(cnt),
+                                  stream);
+      if (rc) return rc;
+    }
+    axpy_kernel<<<grid_for(n2 * kOut), 256, 0, st>>>(y, yk, (float)lk, n2 * kOut, k == 0);
+    NED_LAUNCH_CHECK("axpy_kernel");
+  }
+  assemble_sigma_kernel<<<grid_for(n2), 256, 0, st>>>(cd, md, y, reinterpret_cast<double2*>(sigma_d));
   NED_LAUNCH_CHECK("assemble_sigma_kernel");
   return NEDMFT_OK;
 }

@@ -16,13 +16,20 @@ import torch
 from . import _native as N
 from . import api
 
-N_IN, N_OUT = 14, 2
-DIMS = [14, 256, 256, 256, 256, 2]
+N_IN, N_OUT = 17, 2
+DIMS = [17, 256, 256, 256, 256, 2]
 
 
-def scale(U: float) -> float:
-    """Target scale: the smooth self-energy grows like U^2."""
-    return max(U, 0.05) ** 2 / 8.0
+# Training steps of the network: it learns the discrete X at both, and the
+# warm start extrapolates in dt to the contour it starts (see nedmft.h).
+TRAIN_DTS = (0.1, 0.2)
+# The half-filled model's Mott transition (Sec. III: U > sqrt(2) t* is the
+# insulator).  The features assume that the Green's function settles to a
+# function of t - t' a few units of time after the field is switched on, as a
+# metal's does; plain substitution, the paper's loop, rarely converges on the
+# insulating side within the training runs' iteration budget, so the network
+# has few of its solutions to learn from.
+U_MOTT = 2.0 ** 0.5
 
 
 def init_params(seed: int = 20071101) -> np.ndarray:
@@ -53,25 +60,31 @@ def features(grid: api.Grid, model, device="cuda") -> torch.Tensor:
 
 
 def targets(grid: api.Grid, model, sigma: torch.Tensor) -> torch.Tensor:
+    """X, the impurity Green's function the network learns, from a converged self-energy."""
     t = torch.empty((grid.n_c * grid.n_c, N_OUT), dtype=torch.float32, device=sigma.device)
-    N.check(N.lib().nedmft_mlp_target(ctypes.byref(grid.contour), ctypes.byref(model), _p(sigma), scale(model.U),
-                                      _p(t), _s()))
+    N.check(N.lib().nedmft_mlp_target(ctypes.byref(grid.contour), ctypes.byref(model), _p(sigma), 1.0, _p(t), _s()))
     return t
 
 
-def collect(runs, contour_args, n_quad: int, precision="mixed_bf16", tol=1e-8, max_iter=80, device="cuda"):
-    """Converged plain (zero-start) solves of each (U, E): features and targets stacked.
-
-    Returns (x, t, iterations per run)."""
-    grid = api.contour_grid(*contour_args)
-    xs, ts, its = [], [], []
+def collect(runs, contours, n_quad: int, precision="mixed_bf16", tol=1e-8, max_iter=80, device="cuda"):
+    """Plain (zero-start) solves of each (U, E) on each contour (one per training
+    step); the features and targets of the runs that converged, stacked (a run
+    stopped at max_iter has no fixed point to learn).  Returns (x, t, iterations
+    per run, converged flag per run), runs in the order (U, E) outer, contour inner."""
+    grids = [api.contour_grid(*args) for args in contours]
+    xs, ts, its, conv = [], [], [], []
     for U, E in runs:
         model = api.make_model(U, E)
-        sol = api.dmft_solve(grid, model, n_quad, precision, tol=tol, max_iter=max_iter, device=device)
-        xs.append(features(grid, model, device))
-        ts.append(targets(grid, model, sol.sigma))
-        its.append(sol.iterations)
-    return torch.cat(xs), torch.cat(ts), its
+        for grid in grids:
+            sol = api.dmft_solve(grid, model, n_quad, precision, tol=tol, max_iter=max_iter, device=device)
+            its.append(sol.iterations)
+            conv.append(bool(sol.converged))
+            if sol.converged:
+                xs.append(features(grid, model, device))
+                ts.append(targets(grid, model, sol.sigma))
+    if not xs:
+        raise RuntimeError("collect: no training run converged")
+    return torch.cat(xs), torch.cat(ts), its, conv
 
 
 def loss_and_grad(params: torch.Tensor, x: torch.Tensor, t: torch.Tensor):
@@ -111,17 +124,28 @@ def train(x: torch.Tensor, t: torch.Tensor, steps=2000, batch=2048, lr=1e-3, see
     return p, losses
 
 
-def warm_start(grid: api.Grid, model, params: torch.Tensor) -> torch.Tensor:
-    """Sigma_0 = U w1 delta_c + scale(U) * network(features), complex128 on the device."""
+def warm_start(grid: api.Grid, model, params: torch.Tensor, dts=TRAIN_DTS) -> torch.Tensor:
+    """Sigma_0 from the network's X, extrapolated in dt from the training steps
+    to the grid's own, complex128 on the device."""
     dev = params.device
     sigma = torch.empty((grid.n_c, grid.n_c), dtype=torch.complex128, device=dev)
     ws = api.workspace(N.lib().nedmft_sigma_warm_start_workspace_size(ctypes.byref(grid.contour)), dev)
-    N.check(N.lib().nedmft_sigma_warm_start(ctypes.byref(grid.contour), ctypes.byref(model), _p(params),
-                                            scale(model.U), _p(sigma), _p(ws), ws.numel(), _s()))
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    N.check(N.lib().nedmft_sigma_warm_start(ctypes.byref(grid.contour), ctypes.byref(model), _p(params), len(d),
+                                            d.ctypes.data_as(N.PD), _p(sigma), _p(ws), ws.numel(), _s()))
     return sigma
 
 
 def band_only(grid: api.Grid, model, device="cuda") -> torch.Tensor:
-    """The closed-form band alone (the network's output set to zero)."""
+    """The closed-form part alone, -w1 D (X set to zero): the self-energy of
+    the static U w1 term, the band of the point-split contour delta."""
     zero = torch.zeros(N.lib().nedmft_mlp_param_count(), dtype=torch.float32, device=device)
-    return warm_start(grid, model, zero)
+    return warm_start(grid, model, zero, dts=(grid.contour.dt,))
+
+
+def initial_sigma(grid: api.Grid, model, params: torch.Tensor):
+    """The start the DMFT loop should take: the network's on the metallic side
+    (U < sqrt 2), None (the plain zero start) on the insulating side."""
+    if model.U < U_MOTT:
+        return warm_start(grid, model, params)
+    return None
