@@ -61,6 +61,10 @@ def parse(argv=None):
     ap.add_argument("--tts", action="store_true", help="the full warm-start study only (16 held-out pairs)")
     ap.add_argument("--tts-train-runs", type=int, default=0, help="training runs (0: 16 default run, 64 --tts)")
     ap.add_argument("--tts-eval", type=int, default=0, help="held-out pairs (0: 1 default run, 16 --tts)")
+    ap.add_argument("--config", default="cfg1", choices=["cfg1", "cfg2", "cfg3"],
+                    help="cfg1: the production step (default); cfg2: the ragged sweep of 48 runs with dt -> 0 "
+                         "extrapolation; cfg3: one step of the N_c = 3400 Mott configuration")
+    ap.add_argument("--max-iter", type=int, default=40, help="iteration cap of the cfg2 sweep")
     return ap.parse_args(argv)
 
 
@@ -421,6 +425,107 @@ def time_to_solution(n_train: int, n_eval: int, with_fp64: bool = True):
     return out
 
 
+# ------------------------------------------------------------------ other configurations
+
+
+CFG2 = dict(U=(0.5, 1.0, 1.5, 2.0), E=(0.5, 1.0, 2.0, 4.0), dts=(0.1, 1.0 / 15.0, 0.05), t_min=-5.0, t_max=25.0,
+            beta=10.0, dtau=0.1, n_quad=40)
+CFG3 = dict(t_min=-5.0, t_max=50.0, dt=1.0 / 30.0, beta=10.0, dtau=0.1, U=2.0, E=1.0, n_quad=64)
+
+
+def run_cfg2(args):
+    """The ragged sweep: U in {0.5, 1, 1.5, 2} x E in {0.5, 1, 2, 4} x dt in
+    {0.1, 1/15, 0.05} (N_c = 700 / 1000 / 1300), t in [-5, 25], beta = 10,
+    40 x 40 points, all 48 runs swept together (one iteration of every active
+    run per host synchronisation) to 1e-6 or the iteration cap, then the
+    quadratic dt -> 0 Lagrange extrapolation of every (U, E)'s current in FP64."""
+    import torch
+
+    from paper_0711_0999_gb300 import api
+
+    torch.cuda.set_device(0)
+    C = CFG2
+    pairs = [(U, E) for U in C["U"] for E in C["E"]]
+    grids = {dt: api.contour_grid(C["t_min"], C["t_max"], dt, C["beta"], C["dtau"]) for dt in C["dts"]}
+    runs = [(U, E, dt) for U, E in pairs for dt in C["dts"]]
+    gl = [grids[dt] for _, _, dt in runs]
+    models = [api.make_model(U, E) for U, E, _ in runs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sols = api.dmft_solve_batch(gl, models, C["n_quad"], args.precision, tol=TTS_TOL, max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    t_out = np.arange(C["t_min"], C["t_max"] - 0.2 + 1e-9, 0.2)  # times on all three grids
+    t0 = time.perf_counter()
+    extrap = []
+    for k, (U, E) in enumerate(pairs):
+        cur = [sols[3 * k + r].current for r in range(3)]
+        extrap.append(api.extrapolate_current([grids[dt] for dt in C["dts"]], cur, t_out))
+    torch.cuda.synchronize()
+    t_extrap = time.perf_counter() - t0
+    nq = C["n_quad"] ** 2
+    flops = sum(s.iterations * 8.0 * g.n_c ** 3 * nq for s, g in zip(sols, gl))  # B-form, lattice steps only
+    its = [s.iterations for s in sols]
+    line = {"experiment": "cfg2 ragged sweep", "precision": args.precision, "runs": len(runs),
+            "converged": int(sum(s.converged for s in sols)), "iterations": its, "iteration_cap": args.max_iter,
+            "lattice_steps": int(sum(its)), "solve_s": t_solve, "runs_per_s": len(runs) / t_solve,
+            "lattice_steps_per_s": sum(its) / t_solve, "tflops_lattice_bform": flops / t_solve / 1e12,
+            "extrapolation_s": t_extrap, "extrapolated_pairs": len(pairs),
+            "j_extrapolated_max_abs": [float(e.abs().max()) for e in extrap],
+            "n_c": sorted({g.n_c for g in gl}), "points": nq,
+            "note": "dmft_solve_batch: one iteration of every active run per host sync; each run's points fill "
+                    "its own Gauss-Jordan batches"}
+    print(json.dumps(line), flush=True)
+
+
+def run_cfg3(args):
+    """One DMFT iteration (lattice + impurity step) of the long Mott contour:
+    U = 2, E = 1, t in [-5, 50], dt = 1/30 (N_c = 3400), 64 x 64 points,
+    streamed through the Gauss-Jordan in batches sized to HBM, with the
+    synthetic self-energy workload; one untimed iteration first."""
+    import torch
+
+    from paper_0711_0999_gb300 import _native as N
+    from paper_0711_0999_gb300 import api
+    from paper_0711_0999_gb300.synth import workload_sigma
+
+    torch.cuda.set_device(0)
+    C = CFG3
+    g = api.contour_grid(C["t_min"], C["t_max"], C["dt"], C["beta"], C["dtau"])
+    m = api.make_model(C["U"], C["E"])
+    eps, ebar, wq = api.quadrature_grid(C["n_quad"])
+    dev = torch.device("cuda")
+    sig = torch.as_tensor(workload_sigma(g.t, g.w, C["U"]), device=dev)
+    e_d, b_d, w_d = (torch.as_tensor(a, device=dev) for a in (eps, ebar, wq))
+    ws = api.workspace(api.lattice_workspace_size(g, len(wq), args.precision), dev)
+    ws_imp = api.workspace(N.lib().nedmft_impurity_workspace_size(N.ctypes.byref(g.contour)), dev)
+    out = torch.empty((g.n_c, g.n_c), dtype=torch.complex128, device=dev)
+    st = torch.cuda.current_stream()
+
+    def iteration():
+        api.lattice_gloc(g, m, sig, e_d, b_d, w_d, precision=args.precision, ws=ws, out=out, stream=st)
+        ev[1].record(st)
+        api.impurity_update(g, m, out, sig, ws=ws_imp, stream=st)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    iteration()
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    iteration()
+    ev[2].record(st)
+    torch.cuda.synchronize()
+    api.check_status()
+    lat = ev[0].elapsed_time(ev[1]) / 1e3
+    imp = ev[1].elapsed_time(ev[2]) / 1e3
+    nq = len(wq)
+    line = {"experiment": "cfg3 long contour", "precision": args.precision, "n_c": g.n_c, "points": nq,
+            "points_per_batch": api.lattice_batch(g, nq, args.precision), "lattice_s": lat, "impurity_s": imp,
+            "iteration_s": lat + imp, "solves_per_s": nq / lat,
+            "tflops_lattice_bform": 8.0 * g.n_c ** 3 * nq / lat / 1e12,
+            "workspace_gb": ws.numel() / 1e9}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 
@@ -431,6 +536,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.config == "cfg2":
+        run_cfg2(args)
+        return
+    if args.config == "cfg3":
+        run_cfg3(args)
         return
     if args.tts:
         import torch

@@ -45,7 +45,7 @@ int tuned_batch(const nedmft_contour& c, int nq, nedmft_precision prec) {
 
 int default_batch(const nedmft_contour& c, int nq, Path path) {
   const size_t np = padded_for(path, c.n_c);
-  size_t per = 0, budget = (size_t)40 << 30;  // about 40 GB of batch buffers
+  size_t per = 0, budget = (size_t)96 << 30;  // about 96 GB of batch buffers (a third of HBM)
   int cap = 152;
   switch (path) {
     case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
