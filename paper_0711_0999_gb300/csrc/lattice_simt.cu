@@ -185,25 +185,61 @@ int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* e
 // ------------------------------------------------------------------ blocked Gauss-Jordan, CUDA cores
 
 // Step k of blocked Gauss-Jordan on A (np x np, batch stride np*np):
-//   P = inv(A_KK)                                        gj_pivot_kernel
+//   P = inv(A_KK)                                        gj_pivot32_fp64_kernel
 //   R = P A_{K,:} with R_{:,K} = P;  C = A_{:,K} with C_K = -I   gj_panels_kernel
 //   A <- A(with rows K and columns K zeroed) - C R       gj_update_kernel
-template <class T, int NB>
-__global__ void __launch_bounds__(256) gj_pivot_kernel(cplx_t<T>* __restrict__ A, int np, int k0,
-                                                       cplx_t<T>* __restrict__ Pbuf, int* status) {
-  using C = cplx_t<T>;
-  __shared__ C p[NB * (NB + 1)];
-  __shared__ C col[NB];
-  const int b = blockIdx.x;
-  const C* a = A + (size_t)b * np * np;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, cc = e % NB;
-    p[r * (NB + 1) + cc] = a[(size_t)(k0 + r) * np + k0 + cc];
-  }
+// P = inv(A_KK) for the 32 x 32 FP64 block at (k0, k0) of every matrix: thread
+// t holds row t / 8, columns 4 (t % 8) .. +3 in registers; each step publishes
+// the pivot column, the pivot row and the pivot's inverse through
+// double-buffered shared arrays (written for step k + 1 while step k's are
+// still being read), so one barrier per step.  No pivoting: the caller orders
+// the rows.
+__global__ void __launch_bounds__(256) gj_pivot32_fp64_kernel(const double2* __restrict__ A, int np, int k0,
+                                                              double2* __restrict__ Pbuf, int* status) {
+  __shared__ double2 colb[2][32], rowb[2][32], pinvb[2];
+  __shared__ int bad;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int r = t >> 3, c0 = 4 * (t & 7);
+  const double2* a = A + (size_t)b * np * np + (size_t)(k0 + r) * np + k0 + c0;
+  double2 v[4] = {a[0], a[1], a[2], a[3]};
+  if (t == 0) bad = 0;
+  auto publish = [&](int k, int buf) {
+    const int u = k & 3;  // register selects, not an indexed (local-memory) array
+    const double2 vk = u == 0 ? v[0] : (u == 1 ? v[1] : (u == 2 ? v[2] : v[3]));
+    if ((k >> 2) == (t & 7)) colb[buf][r] = vk;
+    if (r == k) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rowb[buf][c0 + q] = v[q];
+      if ((k >> 2) == (t & 7)) {
+        double2 pinv;
+        if (!cinv_guard<double>(vk, pinv, 1e-12)) bad = 1;
+        pinvb[buf] = pinv;
+      }
+    }
+  };
+  publish(0, 0);
   __syncthreads();
-  smem_gauss_jordan<T>(p, NB, NB + 1, col, sizeof(T) == 8 ? T(1e-12) : T(1e-6), status);
-  C* out = Pbuf + (size_t)b * NB * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = p[(e / NB) * (NB + 1) + e % NB];
+  for (int k = 0; k < 32; ++k) {
+    const int buf = k & 1;
+    const double2 pinv = pinvb[buf];
+    if (r == k) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = (c0 + u == k) ? pinv : cmul(v[u], pinv);
+    } else {
+      const double2 g = cmul(colb[buf][r], pinv);  // a_rk / a_kk
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = c0 + u;
+        v[u] = (j == k) ? make_double2(-g.x, -g.y) : csub(v[u], cmul(g, rowb[buf][j]));
+      }
+    }
+    if (k + 1 < 32) publish(k + 1, buf ^ 1);
+    __syncthreads();
+  }
+  double2* out = Pbuf + (size_t)b * 32 * 32 + (size_t)r * 32 + c0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = v[u];
+  if (t == 0 && bad && status) atomicCAS(status, 0, DS_SINGULAR);
 }
 
 template <class T, int NB>
@@ -306,8 +342,9 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
   const size_t smem = sizeof(cplx_t<T>) * (64 * (NB + 1) + NB * 64);
   NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int k0 = 0; k0 < np; k0 += NB) {
-    gj_pivot_kernel<T, NB><<<nb_batch, 256, 0, st>>>(A, np, k0, Pbuf, status);
-    NED_LAUNCH_CHECK("gj_pivot_kernel");
+    static_assert(NB == 32, "the pivot-block kernel inverts 32 x 32 blocks");
+    gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, Pbuf, status);
+    NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
     gj_panels_kernel<T, NB><<<dim3(np / 32, nb_batch), 256, 0, st>>>(A, np, k0, Pbuf, Rbuf, Cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
     const int slot = instr_begin(st);
@@ -347,8 +384,6 @@ __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restri
                                                          int* __restrict__ piv, int* status) {
   extern __shared__ float2 tp[];  // kTourRows x (kTourNB + 1)
   __shared__ int gidx[kTourRows];
-  __shared__ float bv[kTourRows];
-  __shared__ int bi[kTourRows];
   constexpr int LD = kTourNB + 1;
   const int c = blockIdx.x, t = threadIdx.x;
   const int i = c * kTourRows + t;
@@ -367,39 +402,51 @@ __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restri
   __syncthreads();
   const int nrows = min(kTourRows, in_count - c * kTourRows);
   const int steps = min(ncol, nrows);
+  constexpr int kWarps = kTourRows / 32;
+  __shared__ float wv[kWarps];
+  __shared__ int wi[kWarps];
   for (int j = 0; j < steps; ++j) {
-    // largest |entry| of column j among local rows >= j (ties: lower local index)
+    // largest |entry| of column j among local rows >= j (ties: lower local
+    // index): a shuffle argmax per warp, then every thread over the warps
     float m = -1.f;
     if (t >= j && t < nrows && gidx[t] >= 0) {
       const float2 v = tp[t * LD + j];
       m = v.x * v.x + v.y * v.y;
     }
-    bv[t] = m;
-    bi[t] = t;
-    __syncthreads();
-    for (int s = kTourRows / 2; s > 0; s >>= 1) {
-      if (t < s) {
-        const float o = bv[t + s];
-        const int oi = bi[t + s];
-        if (o > bv[t] || (o == bv[t] && oi < bi[t])) {
-          bv[t] = o;
-          bi[t] = oi;
-        }
+    int idx = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, m, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (om > m || (om == m && oi < idx)) {
+        m = om;
+        idx = oi;
       }
-      __syncthreads();
     }
-    const int p = bi[0];
-    // swap local rows j and p (one thread per column, then the index)
-    if (p != j && t < kTourNB) {
-      const float2 a = tp[j * LD + t];
-      tp[j * LD + t] = tp[p * LD + t];
-      tp[p * LD + t] = a;
+    if ((t & 31) == 0) {
+      wv[t >> 5] = m;
+      wi[t >> 5] = idx;
     }
     __syncthreads();
-    if (t == 0 && p != j) {
-      const int g = gidx[j];
-      gidx[j] = gidx[p];
-      gidx[p] = g;
+    float bm = wv[0];
+    int p = wi[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w)
+      if (wv[w] > bm || (wv[w] == bm && wi[w] < p)) {
+        bm = wv[w];
+        p = wi[w];
+      }
+    // swap local rows j and p (one thread per column, one for the index)
+    if (p != j) {
+      if (t < kTourNB) {
+        const float2 x = tp[j * LD + t];
+        tp[j * LD + t] = tp[p * LD + t];
+        tp[p * LD + t] = x;
+      } else if (t == kTourNB) {
+        const int g = gidx[j];
+        gidx[j] = gidx[p];
+        gidx[p] = g;
+      }
     }
     __syncthreads();
     const float2 pv = tp[j * LD + j];
@@ -551,8 +598,8 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     }
     apply_swaps_kernel<<<(np + 255) / 256, 256, 0, st>>>(ap, np, n, k0, piv);
     NED_LAUNCH_CHECK("apply_swaps_kernel");
-    gj_pivot_kernel<double, NB><<<1, 256, 0, st>>>(ap, np, k0, pbuf, status);
-    NED_LAUNCH_CHECK("gj_pivot_kernel");
+    gj_pivot32_fp64_kernel<<<1, 256, 0, st>>>(ap, np, k0, pbuf, status);
+    NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
     gj_panels_kernel<double, NB><<<dim3(np / 32, 1), 256, 0, st>>>(ap, np, k0, pbuf, rbuf, cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
     gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf);
