@@ -253,14 +253,17 @@ int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
                    nedmft_precision prec, double* j_d, double* j_imag_d,
                    void* ws_d, size_t ws_bytes, void* stream);
 
-/* Batch autotuner (a choice the paper leaves to the machine: how many
- * quadrature points, its independent solves of Sec. II, run at once).  Times one
- * lattice step (after an untimed one) with each candidate number of points
- * per batch that fits the workspace, and records the fastest for this
- * (n_c, nq, prec); later calls of nedmft_lattice_workspace_size(..., batch = 0),
- * nedmft_lattice_gloc, nedmft_current and the DMFT drivers in this process use
- * it.  Tune before sizing workspaces: a workspace sized for the former batch
- * may be too small afterwards (ENOMEM, never an overrun).
+/* Batch autotuner (choices the paper leaves to the machine: how many
+ * quadrature points, its independent solves of Sec. II, run at once, and how
+ * the solves are blocked).  Times one lattice step (after an untimed one) for
+ * every candidate number of points per batch that fits the workspace and, on
+ * the tensor-core path, for each Gauss-Jordan block width that applies (256
+ * columns, the default from 512 padded rows up, and 128, which also pads N_c
+ * to a multiple of 128 instead of 256), and records the fastest pair for this
+ * (n_c, nq, prec); later calls of nedmft_lattice_workspace_size(..., batch =
+ * 0), nedmft_lattice_gloc, nedmft_current and the DMFT drivers in this
+ * process use it.  Tune before sizing workspaces: a workspace sized for the
+ * former choice may be too small afterwards (ENOMEM, never an overrun).
  *   Arguments 1-8 as nedmft_lattice_gloc (Sigma and the points are the ones
  *   to time with); candidates: n_candidates batch sizes on the host;
  *   best_batch, best_ms: host outputs (may be NULL).  Synchronises the stream.
@@ -278,6 +281,22 @@ int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_model* m,
  * nq).  0 for invalid arguments. */
 int32_t nedmft_lattice_batch(const nedmft_contour* c, int32_t nq,
                              nedmft_precision prec);
+
+/* Record a choice for (c, nq, prec) as nedmft_lattice_autotune would: batch
+ * points per batch (0 = the default) and Gauss-Jordan block width (0 = the
+ * default, 128 or 256; 256 applies only where N_c pads to a multiple of 256
+ * from 512 up, otherwise 128 is used).  Same effect on later calls as a tuning
+ * run.  EINVAL for other values. */
+int nedmft_lattice_set_tuning(const nedmft_contour* c, int32_t nq,
+                              nedmft_precision prec, int32_t batch,
+                              int32_t width);
+
+/* Columns per Gauss-Jordan step that nedmft_lattice_gloc uses for (c, nq,
+ * prec): 32 on the FP64 path; 128 or 256 on the tensor-core path (the tuned
+ * width if nedmft_lattice_autotune ran for them, else the default).  0 for
+ * invalid arguments. */
+int32_t nedmft_lattice_block_width(const nedmft_contour* c, int32_t nq,
+                                   nedmft_precision prec);
 
 /* The lattice step for small contours (n_c <= 112), FP64 arithmetic, with
  * no workspace argument and no device allocation of any kind.  The paper has

@@ -96,6 +96,8 @@ SIGNATURES = {
     "nedmft_lattice_autotune": (ctypes.c_int, [PC, PM, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_int,
                                                PI, c_int32, PI, PD, c_void_p, c_size_t, c_void_p]),
     "nedmft_lattice_batch": (c_int32, [PC, c_int32, ctypes.c_int]),
+    "nedmft_lattice_block_width": (c_int32, [PC, c_int32, ctypes.c_int]),
+    "nedmft_lattice_set_tuning": (ctypes.c_int, [PC, c_int32, ctypes.c_int, c_int32, c_int32]),
     "nedmft_dmft_batch_workspace_size": (c_size_t, [c_int32, PC, c_int32, ctypes.c_int]),
     "nedmft_dmft_solve_batch": (ctypes.c_int, [c_int32, PC, PM, c_int32, ctypes.c_int, ctypes.POINTER(c_void_p),
                                                c_double, c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),

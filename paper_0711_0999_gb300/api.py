@@ -212,6 +212,14 @@ def lattice_batch(grid: Grid, nq: int, precision="mixed_bf16") -> int:
     return int(N.lib().nedmft_lattice_batch(ctypes.byref(grid.contour), nq, _prec(precision)))
 
 
+def lattice_set_tuning(grid: Grid, nq: int, precision="mixed_bf16", batch: int = 0, width: int = 0) -> None:
+    N.check(N.lib().nedmft_lattice_set_tuning(ctypes.byref(grid.contour), nq, _prec(precision), batch, width))
+
+
+def lattice_block_width(grid: Grid, nq: int, precision="mixed_bf16") -> int:
+    return int(N.lib().nedmft_lattice_block_width(ctypes.byref(grid.contour), nq, _prec(precision)))
+
+
 def moments(grid: Grid, gloc: torch.Tensor, stream=None):
     """(mu0, mu1, mu2, n) on the upper-branch times: the equal-time moments of G^R and the density."""
     dev = gloc.device

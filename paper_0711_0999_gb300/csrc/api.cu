@@ -31,26 +31,30 @@ Path choose_path(const nedmft_contour& c, nedmft_precision p) {
   return Path::MixedUmma;
 }
 
-int padded_for(Path path, int n) { return path == Path::MixedUmma ? umma_padded(n) : padded(n); }
+int padded_for(Path path, int n, int width) { return path == Path::MixedUmma ? umma_padded(n, width) : padded(n); }
 
-// Batch sizes chosen by nedmft_lattice_autotune, per (n_c, nq, precision).
+// Points per batch and Gauss-Jordan block width chosen by
+// nedmft_lattice_autotune, per (n_c, nq, precision); 0 = the default.
+struct Tuned {
+  int batch, width;
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tuned;
+std::map<std::tuple<int, int, int>, Tuned> g_tuned;
 
-int tuned_batch(const nedmft_contour& c, int nq, nedmft_precision prec) {
+Tuned tuned_for(const nedmft_contour& c, int nq, nedmft_precision prec) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned.find(std::make_tuple(c.n_c, nq, (int)prec));
-  return it == g_tuned.end() ? 0 : it->second;
+  return it == g_tuned.end() ? Tuned{0, 0} : it->second;
 }
 
-int default_batch(const nedmft_contour& c, int nq, Path path) {
-  const size_t np = padded_for(path, c.n_c);
+int default_batch(const nedmft_contour& c, int nq, Path path, int width) {
+  const size_t np = padded_for(path, c.n_c, width);
   size_t per = 0, budget = (size_t)96 << 30;  // about 96 GB of batch buffers (a third of HBM)
   int cap = 152;
   switch (path) {
     case Path::Small64: per = sizeof(double2) * c.n_c * c.n_c; cap = 2048; break;
     case Path::Blocked64: per = sizeof(double2) * np * np; cap = 152; break;
-    case Path::MixedUmma: per = umma_batch_bytes_per_matrix((int)np); cap = umma_default_batch((int)np); break;
+    case Path::MixedUmma: per = umma_batch_bytes_per_matrix((int)np, width); cap = umma_default_batch((int)np); break;
   }
   int b = (int)(budget / (per ? per : 1));
   if (b > cap) b = cap;
@@ -61,16 +65,21 @@ int default_batch(const nedmft_contour& c, int nq, Path path) {
 
 struct LatticeLayout {
   size_t S, gscratch, jacc, batch, pbuf, rbuf, cbuf, extra, total;
-  int np, mb;
+  int np, mb, width;
   Path path;
 };
 
-LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision prec, int batch) {
+// batch <= 0: the tuned batch (else the default); width < 0: the tuned width
+// (else the default, 0)
+LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision prec, int batch, int width = -1) {
   LatticeLayout L{};
   L.path = choose_path(c, prec);
-  L.np = padded_for(L.path, c.n_c);
-  if (batch <= 0) batch = tuned_batch(c, nq, prec);
-  L.mb = batch > 0 ? (batch < nq ? batch : nq) : default_batch(c, nq, L.path);
+  const Tuned t = tuned_for(c, nq, prec);
+  if (width < 0) width = t.width;
+  L.width = width;
+  L.np = padded_for(L.path, c.n_c, width);
+  if (batch <= 0) batch = t.batch;
+  L.mb = batch > 0 ? (batch < nq ? batch : nq) : default_batch(c, nq, L.path, width);
   const size_t n = c.n_c, np = L.np, mb = L.mb;
   L.S = align256(sizeof(double2) * n * n);
   L.gscratch = align256(sizeof(double2) * n * n);
@@ -86,7 +95,7 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
       L.cbuf = align256(sizeof(double2) * np * kNbSimt * mb);
       break;
     case Path::MixedUmma:
-      L.batch = align256(umma_batch_bytes((int)np, (int)mb));
+      L.batch = align256(umma_batch_bytes((int)np, (int)mb, width));
       L.extra = align256(umma_shared_bytes((int)np, nq));
       break;
   }
@@ -99,7 +108,7 @@ LatticeLayout lattice_layout(const nedmft_contour& c, int nq, nedmft_precision p
 // The lattice step proper (also used by the current and the DMFT loop).
 int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
                       const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
-                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts);
+                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts, int width = -1);
 
 int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
                 const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
@@ -107,11 +116,12 @@ int lattice_run(const nedmft_contour& c, const nedmft_model& m, const double2* s
   return lattice_run_batch(c, m, sigma, eps, ebar, wq, nq, prec, gloc, j, ji, ws, ws_bytes, st, 0);
 }
 
-// batch_pts > 0: points per batch (clamped to nq); 0: the tuned or default size
+// batch_pts > 0: points per batch (clamped to nq); 0: the tuned or default
+// size; width >= 0: the Gauss-Jordan block width (0 = default), < 0: the tuned one
 int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const double2* sigma, const double* eps,
                       const double* ebar, const double* wq, int nq, nedmft_precision prec, double2* gloc, double* j,
-                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts) {
-  LatticeLayout L = lattice_layout(c, nq, prec, batch_pts);
+                      double* ji, void* ws, size_t ws_bytes, cudaStream_t st, int batch_pts, int width) {
+  LatticeLayout L = lattice_layout(c, nq, prec, batch_pts, width);
   if (ws_bytes < L.total) return set_error(NEDMFT_ENOMEM, "lattice: workspace %zu < %zu bytes", ws_bytes, L.total);
   int* status = device_status_ptr();
   if (!status) return set_error(NEDMFT_ECUDA, "lattice: no device status word");
@@ -156,7 +166,8 @@ int lattice_run_batch(const nedmft_contour& c, const nedmft_model& m, const doub
         break;
       }
       case Path::MixedUmma: {
-        if ((rc = umma_lattice_batch(cd, md, eps, ebar, wq, q0, nb, nq, np, S, extra, batch, first, gloc, ja, status, st)))
+        if ((rc = umma_lattice_batch(cd, md, eps, ebar, wq, q0, nb, nq, np, S, extra, batch, first, gloc, ja, status, st,
+                                     L.width)))
           return rc;
         break;
       }
@@ -236,28 +247,39 @@ extern "C" int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_mod
   cudaEvent_t e0, e1;
   NED_CUDA(cudaEventCreate(&e0));
   NED_CUDA(cudaEventCreate(&e1));
-  int best = 0;
+  int best = 0, best_w = 0;
   float best_t = 0.f;
+  // block widths to try: the default, and 128 columns where the default is wider
+  // (which also pads to a multiple of 128 instead of 256)
+  int widths[2] = {0, 128};
+  int n_widths = 1;
+  if (choose_path(*c, prec) == Path::MixedUmma) {
+    const int np0 = umma_padded(c->n_c, 0);
+    if (umma_block_width(np0, 0) != 128) n_widths = 2;
+  }
   for (int k = 0; k < n_candidates && !rc; ++k) {
     const int b = candidates[k];
     if (b < 1) continue;
-    if (lattice_layout(*c, nq, prec, b).total > ws_bytes) continue;  // does not fit the workspace
-    // one untimed pass (first-use setup), one timed pass
-    for (int pass = 0; pass < 2 && !rc; ++pass) {
-      if (pass == 1) {
-        const cudaError_t e = cudaEventRecord(e0, st);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
+    for (int wi = 0; wi < n_widths && !rc; ++wi) {
+      const int w = widths[wi];
+      if (lattice_layout(*c, nq, prec, b, w).total > ws_bytes) continue;  // does not fit the workspace
+      // one untimed pass (first-use setup), one timed pass
+      for (int pass = 0; pass < 2 && !rc; ++pass) {
+        if (pass == 1) {
+          const cudaError_t e = cudaEventRecord(e0, st);
+          if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
+        }
+        rc = lattice_run_batch(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec,
+                               nullptr, nullptr, nullptr, ws_d, ws_bytes, st, b, w);
       }
-      rc = lattice_run_batch(*c, *m, reinterpret_cast<const double2*>(sigma_d), eps_d, ebar_d, wq_d, nq, prec,
-                             nullptr, nullptr, nullptr, ws_d, ws_bytes, st, b);
+      if (rc) break;
+      cudaError_t e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+      if (!best || ms < best_t) { best = b < nq ? b : nq; best_w = w; best_t = ms; }
     }
-    if (rc) break;
-    cudaError_t e = cudaEventRecord(e1, st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
-    if (!best || ms < best_t) { best = b < nq ? b : nq; best_t = ms; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -265,7 +287,7 @@ extern "C" int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_mod
   if (!best) return set_error(NEDMFT_ENOMEM, "autotune: no candidate batch fits the workspace of %zu bytes", ws_bytes);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[std::make_tuple(c->n_c, (int)nq, (int)prec)] = best;
+    g_tuned[std::make_tuple(c->n_c, (int)nq, (int)prec)] = Tuned{best, best_w};
   }
   if (best_batch) *best_batch = best;
   if (best_ms) *best_ms = best_t;
@@ -276,4 +298,23 @@ extern "C" int32_t nedmft_lattice_batch(const nedmft_contour* c, int32_t nq, ned
   if (!valid_contour(c) || nq < 1) return 0;
   if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16) return 0;
   return lattice_layout(*c, nq, prec, 0).mb;
+}
+
+extern "C" int nedmft_lattice_set_tuning(const nedmft_contour* c, int32_t nq, nedmft_precision prec, int32_t batch,
+                                         int32_t width) {
+  if (!valid_contour(c) || nq < 1) return set_error(NEDMFT_EINVAL, "set_tuning: invalid contour or nq");
+  if (prec != NEDMFT_FP64 && prec != NEDMFT_MIXED_BF16) return set_error(NEDMFT_EINVAL, "set_tuning: precision");
+  if (batch < 0 || (width != 0 && width != 128 && width != 256))
+    return set_error(NEDMFT_EINVAL, "set_tuning: batch %d < 0 or width %d not 0, 128 or 256", batch, width);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[std::make_tuple(c->n_c, (int)nq, (int)prec)] = Tuned{batch, width};
+  return NEDMFT_OK;
+}
+
+extern "C" int32_t nedmft_lattice_block_width(const nedmft_contour* c, int32_t nq, nedmft_precision prec) {
+  if (!valid_contour(c) || nq < 1) return 0;
+  if (prec == NEDMFT_FP64) return 32;
+  if (prec != NEDMFT_MIXED_BF16) return 0;
+  const LatticeLayout L = lattice_layout(*c, nq, prec, 0);
+  return umma_block_width(L.np, L.width);
 }

@@ -1147,10 +1147,18 @@ GjBuffers gj_buffers(int np) {
   return g;
 }
 
-// Block width of the tensor-core Gauss-Jordan for padded size np.
-int gj_width(int np) { return (np >= 512 && np % 256 == 0) ? 256 : 128; }
+// Block width of the tensor-core Gauss-Jordan for padded size np: `width`
+// 128 or 256 if the caller chose one (256 needs np a multiple of 256, from
+// 512 up), else 256 where it fits and 128 below.
+int gj_width(int np, int width) {
+  const bool w256 = np >= 512 && np % 256 == 0;
+  if (width == 128) return 128;
+  return w256 ? 256 : 128;
+}
 
-GjBuffers gj_buffers_for(int np) { return gj_width(np) == 256 ? gj_buffers<256>(np) : gj_buffers<128>(np); }
+GjBuffers gj_buffers_for(int np, int width) {
+  return gj_width(np, width) == 256 ? gj_buffers<256>(np) : gj_buffers<128>(np);
+}
 
 }  // namespace
 
@@ -1302,8 +1310,8 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
 
 }  // namespace
 
-int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st) {
-  return gj_width(np) == 256 ? gj_blocked_umma_w<256>(A, n, np, nb, scratch, status, st, true)
+int gj_blocked_umma(float2* A, int n, int np, int nb, char* scratch, int* status, cudaStream_t st, int width) {
+  return gj_width(np, width) == 256 ? gj_blocked_umma_w<256>(A, n, np, nb, scratch, status, st, true)
                              : gj_blocked_umma_w<128>(A, n, np, nb, scratch, status, st, true);
 }
 
@@ -2055,14 +2063,21 @@ size_t flags_bytes(int nq) { return align1k(sizeof(int) * (size_t)nq); }
 
 // ------------------------------------------------------------------ lattice batch on this path
 
-int umma_padded(int n) { return n > 512 ? ((n + 255) / 256) * 256 : ((n + 127) / 128) * 128; }
-size_t umma_batch_bytes_per_matrix(int np) { return gj_buffers_for(np).total + refine_layout(np, 1).total; }
+int umma_block_width(int np, int width) { return gj_width(np, width); }
+int umma_padded(int n, int width) {
+  return (n > 512 && width != 128) ? ((n + 255) / 256) * 256 : ((n + 127) / 128) * 128;
+}
+size_t umma_batch_bytes_per_matrix(int np, int width) {
+  return gj_buffers_for(np, width).total + refine_layout(np, 1).total;
+}
 int umma_default_batch(int np) { return np <= 2048 ? 152 : 76; }
 size_t umma_shared_bytes(int np, int nq) {
   return align1k(kOzS * sizeof(__nv_bfloat16) * (size_t)np * 2 * np) + align1k(sizeof(int) * (size_t)np) +
          flags_bytes(nq) + align1k(sizeof(float2) * (size_t)np * np);
 }
-size_t umma_batch_bytes(int np, int nb) { return gj_buffers_for(np).total * nb + refine_layout(np, nb).total; }
+size_t umma_batch_bytes(int np, int nb, int width) {
+  return gj_buffers_for(np, width).total * nb + refine_layout(np, nb).total;
+}
 
 int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
                         const double* wq, int nq, char* shared, cudaStream_t st) {
@@ -2096,8 +2111,9 @@ int encode_oz_map(CUtensorMap* map, void* base, uint64_t tiles, uint32_t rgroups
 
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
                        const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
-                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st) {
-  const GjBuffers g = gj_buffers_for(np);
+                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st,
+                       int width) {
+  const GjBuffers g = gj_buffers_for(np, width);
   const RefineShared sh = shared_layout(shared, np, nq_total);
   const int mb_alloc = nb;  // regions are sized for this batch by the caller's layout
   (void)mb_alloc;
@@ -2117,7 +2133,7 @@ int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps
   int rc;
   gen_a_fast_kernel<<<dim3(np / kGenRows, nb), 256, 0, st>>>(c, m, eps, ebar, q0, sh.base, X, np);
   NED_LAUNCH_CHECK("gen_a_fast_kernel");
-  if ((rc = gj_blocked_umma(X, c.n, np, nb, scratch, status, st))) return rc;
+  if ((rc = gj_blocked_umma(X, c.n, np, nb, scratch, status, st, width))) return rc;
   oz_coef_kernel<<<dim3((np + 255) / 256, nb), 256, 0, st>>>(c, m, eps, ebar, q0, S, np, coef, sh.flags);
   NED_LAUNCH_CHECK("oz_coef_kernel");
   oz_pack_x_kernel<<<dim3(np / 32, nb), 256, 0, st>>>(X, np, q0, sh.flags, ximg, xexp, aimg);

@@ -6,17 +6,21 @@
 
 namespace nedmft {
 
-// padded size for this path: a multiple of 128, of 256 above 512 (wider Gauss-Jordan blocks)
-int umma_padded(int n);
-size_t umma_batch_bytes_per_matrix(int np);
-size_t umma_batch_bytes(int np, int nb);
+// Gauss-Jordan block width of this path: 0 = the default (256 columns where
+// the padded size is a multiple of 256 from 512 up, else 128), or 128 / 256.
+// Padded size: a multiple of 128, of 256 above 512 unless the width is 128.
+int umma_padded(int n, int width);
+int umma_block_width(int np, int width);  // the width the path uses for padded size np
+size_t umma_batch_bytes_per_matrix(int np, int width);
+size_t umma_batch_bytes(int np, int nb, int width);
 int umma_default_batch(int np);
 size_t umma_shared_bytes(int np, int nq);
 int umma_prepare_shared(const ContourDev& c, const double2* S, int np, const double* eps, const double* ebar,
                         const double* wq, int nq, char* shared, cudaStream_t st);
 int umma_lattice_batch(const ContourDev& c, const ModelDev& m, const double* eps, const double* ebar,
                        const double* wq, int q0, int nb, int nq_total, int np, const double2* S, char* shared,
-                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st);
+                       char* batch, bool first, double2* gloc, double2* jacc, int* status, cudaStream_t st,
+                       int width);
 
 // Limit of the bounded device waits on the current device (synchronises st).
 int umma_set_wait_ns(uint64_t ns, cudaStream_t st);

@@ -80,3 +80,30 @@ def test_mixed_run_batch_matches_the_oracle():
         g = s.gloc.cpu().numpy()
         assert np.abs(g - ref.gloc).max() < 1e-6 * np.abs(ref.gloc).max()
         assert np.abs(s.current.cpu().numpy() - ref.current.real).max() < 1e-5
+
+
+def test_block_width_choice_pads_and_solves_correctly():
+    # N_c = 620: the default pads to 768 and inverts in 256-column steps; the
+    # 128-column choice pads to 640; both match the oracle, and the autotuner
+    # records one of the (batch, width) pairs it tried
+    args = (-2, 12.5, 0.05, 4.0, 0.1)
+    c = O.contour_grid(*args)
+    g = api.contour_grid(*args)
+    assert g.n_c == 620
+    m = api.make_model(1.0, 1.5)
+    from paper_0711_0999_gb300.synth import workload_sigma
+    sig = workload_sigma(c.t, c.w, 1.0, seed=8)
+    eps, ebar, wq = O.quadrature_points(3)
+    ref, jref = O.lattice_gloc(c, O.Model(U=1.0, E=1.5), sig, eps, ebar, wq)
+    s = torch.as_tensor(sig, device="cuda")
+    assert api.lattice_block_width(g, 9) == 256
+    for width in (256, 128):
+        api.lattice_set_tuning(g, 9, "mixed_bf16", batch=0, width=width)
+        assert api.lattice_block_width(g, 9) == width
+        gl, j, _ = api.lattice_gloc(g, m, s, eps, ebar, wq, precision="mixed_bf16")
+        torch.cuda.synchronize()
+        api.check_status()
+        assert np.abs(gl.cpu().numpy() - ref).max() < 1e-6 * np.abs(ref).max(), width
+        assert np.abs(j.cpu().numpy() - jref.real).max() < 1e-5, width
+    best, ms = api.lattice_autotune(g, m, s, eps, ebar, wq, "mixed_bf16", candidates=[5, 9])
+    assert best in (5, 9) and ms > 0 and api.lattice_block_width(g, 9) in (128, 256)
