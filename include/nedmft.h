@@ -257,9 +257,10 @@ int nedmft_current(const nedmft_contour* c, const nedmft_model* m,
  * quadrature points, its independent solves of Sec. II, run at once, and how
  * the solves are blocked).  Times one lattice step (after an untimed one) for
  * every candidate number of points per batch that fits the workspace and, on
- * the tensor-core path, for each Gauss-Jordan block width that applies (256
- * columns, the default from 512 padded rows up, and 128, which also pads N_c
- * to a multiple of 128 instead of 256), and records the fastest pair for this
+ * the tensor-core path above 512 rows, for both Gauss-Jordan block widths
+ * (256 columns with N_c padded to a multiple of 256, 128 with a multiple of
+ * 128; by default the library takes 128 only where that padding saves more
+ * than a fifth of the flops), and records the fastest pair for this
  * (n_c, nq, prec); later calls of nedmft_lattice_workspace_size(..., batch =
  * 0), nedmft_lattice_gloc, nedmft_current and the DMFT drivers in this
  * process use it.  Tune before sizing workspaces: a workspace sized for the

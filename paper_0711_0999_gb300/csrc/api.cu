@@ -249,13 +249,14 @@ extern "C" int nedmft_lattice_autotune(const nedmft_contour* c, const nedmft_mod
   NED_CUDA(cudaEventCreate(&e1));
   int best = 0, best_w = 0;
   float best_t = 0.f;
-  // block widths to try: the default, and 128 columns where the default is wider
-  // (which also pads to a multiple of 128 instead of 256)
-  int widths[2] = {0, 128};
+  // block widths to try on the tensor-core path above 512 rows: 256 and 128
+  // columns (the latter also pads to a multiple of 128 instead of 256)
+  int widths[2] = {0, 0};
   int n_widths = 1;
-  if (choose_path(*c, prec) == Path::MixedUmma) {
-    const int np0 = umma_padded(c->n_c, 0);
-    if (umma_block_width(np0, 0) != 128) n_widths = 2;
+  if (choose_path(*c, prec) == Path::MixedUmma && c->n_c > 512) {
+    widths[0] = 256;
+    widths[1] = 128;
+    n_widths = 2;
   }
   for (int k = 0; k < n_candidates && !rc; ++k) {
     const int b = candidates[k];

@@ -6,9 +6,11 @@
 
 namespace nedmft {
 
-// Gauss-Jordan block width of this path: 0 = the default (256 columns where
-// the padded size is a multiple of 256 from 512 up, else 128), or 128 / 256.
-// Padded size: a multiple of 128, of 256 above 512 unless the width is 128.
+// Gauss-Jordan block width of this path: 128 or 256 columns, or 0 for the
+// default (256 where the padded size is a multiple of 256 from 512 up, else
+// 128).  Padded size: a multiple of 128 up to 512; above, a multiple of 256
+// for width 256, of 128 for width 128, and for the default whichever of the
+// two the flop count favours (see umma_padded).
 int umma_padded(int n, int width);
 int umma_block_width(int np, int width);  // the width the path uses for padded size np
 size_t umma_batch_bytes_per_matrix(int np, int width);

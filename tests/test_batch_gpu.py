@@ -83,9 +83,9 @@ def test_mixed_run_batch_matches_the_oracle():
 
 
 def test_block_width_choice_pads_and_solves_correctly():
-    # N_c = 620: the default pads to 768 and inverts in 256-column steps; the
-    # 128-column choice pads to 640; both match the oracle, and the autotuner
-    # records one of the (batch, width) pairs it tried
+    # N_c = 620: 256-column steps pad to 768, 128-column steps to 640 (the
+    # default here); both match the oracle, and the autotuner records one of
+    # the (batch, width) pairs it tried
     args = (-2, 12.5, 0.05, 4.0, 0.1)
     c = O.contour_grid(*args)
     g = api.contour_grid(*args)
@@ -96,7 +96,7 @@ def test_block_width_choice_pads_and_solves_correctly():
     eps, ebar, wq = O.quadrature_points(3)
     ref, jref = O.lattice_gloc(c, O.Model(U=1.0, E=1.5), sig, eps, ebar, wq)
     s = torch.as_tensor(sig, device="cuda")
-    assert api.lattice_block_width(g, 9) == 256
+    assert api.lattice_block_width(g, 9) == 128  # 640 vs 768 rows: (5/6)^3 < 0.8, the default pads to 128
     for width in (256, 128):
         api.lattice_set_tuning(g, 9, "mixed_bf16", batch=0, width=width)
         assert api.lattice_block_width(g, 9) == width
@@ -107,3 +107,13 @@ def test_block_width_choice_pads_and_solves_correctly():
         assert np.abs(j.cpu().numpy() - jref.real).max() < 1e-5, width
     best, ms = api.lattice_autotune(g, m, s, eps, ebar, wq, "mixed_bf16", candidates=[5, 9])
     assert best in (5, 9) and ms > 0 and api.lattice_block_width(g, 9) in (128, 256)
+
+
+def test_default_width_follows_the_padding():
+    # N_c = 1300 pads to 1408 with 128-column steps (0.77 of the flops of 1536): the default takes them;
+    # N_c = 1500 pads to 1536 either way: 256
+    g1300 = api.contour_grid(-5, 25, 0.05, 10.0, 0.1)
+    g1500 = api.contour_grid(-5, 30, 0.05, 10.0, 0.1)
+    assert g1300.n_c == 1300 and g1500.n_c == 1500
+    assert api.lattice_block_width(g1300, 1600) == 128
+    assert api.lattice_block_width(g1500, 2809) == 256
