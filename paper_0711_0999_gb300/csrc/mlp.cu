@@ -7,11 +7,12 @@
 // factors of the step sizes at the ends of the branches.  A small MLP maps
 // (U, E, dt, t, t') to X(t, t'); the self-energy follows from the identity
 // above.  Forward, backward (mean-squared error) and Adam are
-// hand-written kernels; GEMM operands are rounded to bf16 and accumulated in
-// FP32, weights and optimizer state are FP32.
+// hand-written kernels; the GEMMs run on the tensor cores (tcgen05, operands
+// rounded to bf16, FP32 sums in TMEM), weights and optimizer state are FP32.
 #include <math.h>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace nedmft {
 namespace {
@@ -29,69 +30,29 @@ constexpr size_t w_off(int l) {  // host only: offsets are passed to kernels as 
 }
 constexpr size_t kParams = w_off(kLayers);
 
-__device__ __forceinline__ float bf16r(float x) {  // round to the nearest bf16 value
-  uint32_t u = __float_as_uint(x);
-  const uint32_t lsb = (u >> 16) & 1u;
-  u += 0x7fffu + lsb;
-  return __uint_as_float(u & 0xffff0000u);
+// Largest K split of a weight-gradient GEMM (K = samples): enough CTAs to
+// cover the 152 SMs when C has one or two 128-row tiles.
+constexpr int kMaxSplits = 152;
+int splits_for(int m, int k) {
+  const int tiles = (m + 127) / 128, chunks = (k + 63) / 64;
+  const int s = kMaxSplits / tiles;
+  return s < chunks ? s : chunks;
 }
-
-// C[m x n] = op(A) op(B) (+ bias[n]) with A m x k (ta: A stored k x m) and
-// B k x n (tb: B stored n x k), FP32 in memory, bf16-rounded operands, FP32
-// accumulation.  64 x 64 tiles, 256 threads.
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) mlp_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                       const float* __restrict__ bias, float* __restrict__ C, int m,
-                                                       int n, int k, bool accumulate) {
-  __shared__ float as[16][65], bs[16][65];
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < k; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      const int kk = e / 64, ii = e % 64;
-      const int gi = i0 + ii, gk = k0 + kk;
-      float va = 0.f;
-      if (gi < m && gk < k) va = TA ? A[(size_t)gk * m + gi] : A[(size_t)gi * k + gk];
-      as[kk][ii] = bf16r(va);
-      const int gj = j0 + ii;
-      float vb = 0.f;
-      if (gj < n && gk < k) vb = TB ? B[(size_t)gj * k + gk] : B[(size_t)gk * n + gj];
-      bs[kk][ii] = bf16r(vb);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = as[kk][ty + 16 * r];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = bs[kk][tx + 16 * q];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], b[q], acc[r][q]);
-    }
-    __syncthreads();
+size_t split_bytes() {  // the largest split buffer over the layers
+  size_t b = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const size_t x = umma_mlp_split_bytes(kDims[l], kDims[l + 1], kMaxSplits / ((kDims[l] + 127) / 128));
+    b = x > b ? x : b;
   }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * q;
-      if (gi < m && gj < n) {
-        float v = acc[r][q] + (bias ? bias[gj] : 0.f);
-        if (accumulate) v += C[(size_t)gi * n + gj];
-        C[(size_t)gi * n + gj] = v;
-      }
-    }
+  return b;
 }
 
+// C = op(A) op(B) (+ bias) on the tensor cores (bf16 operands, FP32 sums);
+// `part` (split_bytes) lets the weight gradients split their long K.
 template <bool TA, bool TB>
-int gemm(const float* A, const float* B, const float* bias, float* C, int m, int n, int k, bool acc, cudaStream_t st) {
-  mlp_gemm_kernel<TA, TB><<<dim3(ceil_div(n, 64), ceil_div(m, 64)), 256, 0, st>>>(A, B, bias, C, m, n, k, acc);
-  NED_LAUNCH_CHECK("mlp_gemm_kernel");
-  return NEDMFT_OK;
+int gemm(const float* A, const float* B, const float* bias, float* C, int m, int n, int k, bool acc, cudaStream_t st,
+         float* part = nullptr) {
+  return umma_mlp_gemm(A, B, bias, C, m, n, k, TA, TB, acc, part, part ? splits_for(m, k) : 1, st);
 }
 
 __global__ void tanh_kernel(float* __restrict__ h, size_t n) {
@@ -259,8 +220,8 @@ extern "C" int32_t nedmft_mlp_param_count(void) { return (int32_t)kParams; }
 
 extern "C" size_t nedmft_mlp_workspace_size(int32_t n) {
   if (n < 1) return 0;
-  // activations + their gradients (2 x act) + loss partials
-  return align256(sizeof(float) * act_floats(n)) * 2 + align256(sizeof(double) * 152 * 16);
+  // activations + their gradients (2 x act) + loss partials + K-split sums
+  return align256(sizeof(float) * act_floats(n)) * 2 + align256(sizeof(double) * 152 * 16) + align256(split_bytes());
 }
 
 extern "C" int nedmft_mlp_forward(const float* params_d, const float* x_d, int32_t n, float* y_d, void* ws_d,
@@ -295,6 +256,8 @@ extern "C" int nedmft_mlp_grad(const float* params_d, const float* x_d, const fl
   float* act = reinterpret_cast<float*>(p);
   float* dact = reinterpret_cast<float*>(p + align256(sizeof(float) * act_floats(n)));
   double* part = reinterpret_cast<double*>(p + 2 * align256(sizeof(float) * act_floats(n)));
+  float* ksplit = reinterpret_cast<float*>(p + 2 * align256(sizeof(float) * act_floats(n)) +
+                                           align256(sizeof(double) * 152 * 16));
   float* H[kLayers];
   float* D[kLayers];
   for (int l = 0; l < kLayers; ++l) {
@@ -326,7 +289,7 @@ extern "C" int nedmft_mlp_grad(const float* params_d, const float* x_d, const fl
     float* gb = gW + (size_t)kDims[l] * kDims[l + 1];
     const float* xin = l == 0 ? x_d : H[l - 1];
     // dW = xin^T D[l], db = column sums of D[l]
-    int rc = gemm<true, false>(xin, D[l], nullptr, gW, kDims[l], kDims[l + 1], n, false, st);
+    int rc = gemm<true, false>(xin, D[l], nullptr, gW, kDims[l], kDims[l + 1], n, false, st, ksplit);
     if (rc) return rc;
     bias_grad_kernel<<<ceil_div(kDims[l + 1], 128), 128, 0, st>>>(D[l], n, kDims[l + 1], gb);
     NED_LAUNCH_CHECK("bias_grad_kernel");

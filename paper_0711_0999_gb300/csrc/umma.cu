@@ -2239,3 +2239,175 @@ int umma_set_wait_ns(uint64_t ns, cudaStream_t st) {
 }
 
 }  // namespace nedmft
+
+// ------------------------------------------------------------------ small GEMMs of the warm-start network
+//
+// C[m x n] = op(A) op(B) (+ bias[n]) (+ C), FP32 in memory: op(A) is m x k
+// (ta: A stored k x m, else m x k, both row-major), op(B) is k x n (tb: B
+// stored n x k, else k x n).  Each CTA takes 128 rows of C and all n <= 256
+// columns; the operands of a 64-deep K chunk are rounded to bf16 into shared
+// memory in the canonical K-major layout by all 128 threads (zeros past m, n
+// and k), one thread issues the tcgen05 products (M = 128, N = n rounded up
+// to 16) into an FP32 TMEM accumulator, two chunk buffers alternate.  With
+// gridDim.y > 1 each CTA sums a contiguous part of K into its own slice of
+// `part` (m x n each) and mlp_split_reduce_kernel adds the slices in order.
+namespace nedmft {
+namespace {
+
+constexpr int kMlpK = 64;  // K per chunk
+
+__global__ void __launch_bounds__(128, 1)
+    mlp_umma_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B, const float* __restrict__ bias,
+                         float* __restrict__ C, float* __restrict__ part, int m, int n, int k, bool ta, bool tb,
+                         bool accumulate, int chunks_per_split, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int np16 = (n + 15) & ~15;
+  const int nrows_b = (np16 + 127) & ~127;  // B rows held (1 or 2 tiles of 128)
+  const int a_bytes = kTileBytes, b_bytes = nrows_b / 128 * kTileBytes;
+  const int stage = a_bytes + b_bytes;
+  uint64_t* done = reinterpret_cast<uint64_t*>(smem + 2 * stage);  // [2] chunk products complete, [2] all complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int row0 = blockIdx.x * 128;
+  const int nchunks = (k + kMlpK - 1) / kMlpK;
+  const int c_begin = blockIdx.y * chunks_per_split;
+  const int c_end = min(nchunks, c_begin + chunks_per_split);
+  uint32_t cols = 32;
+  while ((int)cols < np16) cols <<= 1;
+  if (t == 0) {
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    mbar_init(&done[2], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_bf16(128, np16);
+  bool ok = true;
+  int issued = 0;
+  for (int c = c_begin; c < c_end; ++c) {
+    const int s = (c - c_begin) & 1;
+    unsigned char* st = smem + s * stage;
+    if (c - c_begin >= 2) {  // the products that read this buffer two chunks ago are done
+      if (!__syncthreads_and(mbar_wait(&done[s], (((c - c_begin) >> 1) - 1) & 1, abort_flag))) { ok = false; break; }
+    }
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(st);
+    __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(st + a_bytes);
+    const int k0 = c * kMlpK;
+    for (int e = t; e < 128 * kMlpK; e += 128) {
+      const int r = ta ? (e & 127) : (e >> 6), kk = ta ? (e >> 7) : (e & 63);
+      const int gr = row0 + r, gk = k0 + kk;
+      float v = 0.f;
+      if (gr < m && gk < k) v = ta ? A[(size_t)gk * m + gr] : A[(size_t)gr * k + gk];
+      sa[img_offset(r, kk, 1)] = __float2bfloat16_rn(v);
+    }
+    for (int e = t; e < nrows_b * kMlpK; e += 128) {
+      const int j = tb ? (e >> 6) : (e % nrows_b), kk = tb ? (e & 63) : (e / nrows_b);
+      const int gk = k0 + kk;
+      float v = 0.f;
+      if (j < n && gk < k) v = tb ? B[(size_t)j * k + gk] : B[(size_t)gk * n + j];
+      sb[img_offset(j, kk, 1)] = __float2bfloat16_rn(v);
+    }
+    fence_proxy_async();  // the generic stores above become visible to the tensor core
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t a_addr = smem_u32(sa), b_addr = smem_u32(sb);
+#pragma unroll
+      for (int kk = 0; kk < kMlpK / 16; ++kk)
+        mma_bf16(tmem, smem_desc(a_addr + kk * 256, 128, 1024), smem_desc(b_addr + kk * 256, 128, 1024), idesc,
+                 (c > c_begin || kk > 0) ? 1u : 0u);
+      mma_commit(&done[s]);
+    }
+    ++issued;
+  }
+  if (t == 0) mma_commit(&done[2]);  // after every product issued above (also after an abort)
+  // every thread: the accumulator is complete (bounded by the drain limit)
+  {
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(&done[2], 0) && global_ns() - t0 < kDrainNs) {
+    }
+  }
+  tc_fence_after();
+  if (ok && issued > 0) {
+    const int r = row0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < np16; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (r < m) {
+        if (gridDim.y > 1) {
+          float* out = part + ((size_t)blockIdx.y * m + r) * n;
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (c0 + e < n) out[c0 + e] = v[e];
+        } else {
+          float* out = C + (size_t)r * n;
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (c0 + e < n) {
+              float x = v[e] + (bias ? bias[c0 + e] : 0.f);
+              if (accumulate) x += out[c0 + e];
+              out[c0 + e] = x;
+            }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, cols);
+  }
+  if (t == 0 && *abort_flag && status) atomicCAS(status, 0, DS_TIMEOUT);
+}
+
+// C = sum over the slices of part (in order) (+ bias) (+ C)
+__global__ void mlp_split_reduce_kernel(const float* __restrict__ part, int splits, const float* __restrict__ bias,
+                                        float* __restrict__ C, int m, int n, bool accumulate) {
+  const size_t total = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    float x = 0.f;
+    for (int s = 0; s < splits; ++s) x += part[(size_t)s * total + e];
+    if (bias) x += bias[e % n];
+    if (accumulate) x += C[e];
+    C[e] = x;
+  }
+}
+
+}  // namespace
+
+size_t umma_mlp_split_bytes(int m, int n, int splits) { return sizeof(float) * (size_t)m * n * splits; }
+
+int umma_mlp_gemm(const float* A, const float* B, const float* bias, float* C, int m, int n, int k, bool ta, bool tb,
+                  bool accumulate, float* part, int splits, cudaStream_t st) {
+  if (n < 1 || n > 256 || m < 1 || k < 1) return set_error(NEDMFT_EINVAL, "mlp gemm: shape %d x %d x %d", m, n, k);
+  const int nchunks = (k + kMlpK - 1) / kMlpK;
+  if (splits < 1 || !part) splits = 1;
+  if (splits > nchunks) splits = nchunks;
+  const int cps = (nchunks + splits - 1) / splits;
+  splits = (nchunks + cps - 1) / cps;
+  const int np16 = (n + 15) & ~15, nrows_b = (np16 + 127) & ~127;
+  const int smem = 2 * (kTileBytes + nrows_b / 128 * kTileBytes) + 1024 + 64;
+  int rc = ensure_dyn_smem(reinterpret_cast<const void*>(mlp_umma_gemm_kernel), smem);
+  if (rc) return rc;
+  int* status = device_status_ptr();
+  mlp_umma_gemm_kernel<<<dim3((m + 127) / 128, splits), 128, smem, st>>>(A, B, bias, C, part, m, n, k, ta, tb,
+                                                                        accumulate, cps, status);
+  NED_LAUNCH_CHECK("mlp_umma_gemm_kernel");
+  if (splits > 1) {
+    const size_t total = (size_t)m * n;
+    const int blocks = (int)((total + 255) / 256 < 1216 ? (total + 255) / 256 : 1216);
+    mlp_split_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, bias, C, m, n, accumulate);
+    NED_LAUNCH_CHECK("mlp_split_reduce_kernel");
+  }
+  return NEDMFT_OK;
+}
+
+}  // namespace nedmft

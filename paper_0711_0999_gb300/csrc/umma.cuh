@@ -30,4 +30,11 @@ int umma_set_wait_ns(uint64_t ns, cudaStream_t st);
 // A bounded wait on a barrier that nothing arrives at (records DS_TIMEOUT).
 int umma_wait_selftest(int* status, cudaStream_t st);
 
+// C[m x n] = op(A) op(B) (+ bias) (+ C) for the warm-start network, FP32 in
+// memory, bf16 tcgen05 products with FP32 sums; n <= 256.  splits > 1 sums K
+// in that many parts into `part` (umma_mlp_split_bytes) and adds them in order.
+size_t umma_mlp_split_bytes(int m, int n, int splits);
+int umma_mlp_gemm(const float* A, const float* B, const float* bias, float* C, int m, int n, int k, bool ta, bool tb,
+                  bool accumulate, float* part, int splits, cudaStream_t st);
+
 }  // namespace nedmft

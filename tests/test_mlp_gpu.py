@@ -20,11 +20,12 @@ def built():
     build_library()
 
 
-def test_gradient_matches_cpu_restatement():
+@pytest.mark.parametrize("n", [300, 5000])  # 3 and 40 row tiles of 128 with a ragged tail; 5 and 79 K chunks of 64
+def test_gradient_matches_cpu_restatement(n):
     p = warmstart.init_params(3)
     rng = np.random.default_rng(4)
-    x = rng.normal(size=(300, 17)).astype(np.float32)  # not a multiple of the 64-row tiles
-    t = rng.normal(size=(300, 2)).astype(np.float32)
+    x = rng.normal(size=(n, 17)).astype(np.float32)
+    t = rng.normal(size=(n, 2)).astype(np.float32)
     loss, g = warmstart.loss_and_grad(torch.as_tensor(p, device="cuda"), torch.as_tensor(x, device="cuda"),
                                       torch.as_tensor(t, device="cuda"))
     g = g.cpu().numpy().astype(np.float64)
