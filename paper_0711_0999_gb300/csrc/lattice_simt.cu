@@ -193,14 +193,18 @@ int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* e
 // the pivot column, the pivot row and the pivot's inverse through
 // double-buffered shared arrays (written for step k + 1 while step k's are
 // still being read), so one barrier per step.  No pivoting: the caller orders
-// the rows.
+// the rows.  Row r of the block is matrix row rows[r] when `rows` is given
+// and rows[r] >= 0 (the pivot rows of a step before they are swapped into
+// place), else k0 + r.
 __global__ void __launch_bounds__(256) gj_pivot32_fp64_kernel(const double2* __restrict__ A, int np, int k0,
+                                                              const int* __restrict__ rows,
                                                               double2* __restrict__ Pbuf, int* status) {
   __shared__ double2 colb[2][32], rowb[2][32], pinvb[2];
   __shared__ int bad;
   const int b = blockIdx.x, t = threadIdx.x;
   const int r = t >> 3, c0 = 4 * (t & 7);
-  const double2* a = A + (size_t)b * np * np + (size_t)(k0 + r) * np + k0 + c0;
+  const int src = (rows && rows[r] >= 0) ? rows[r] : k0 + r;
+  const double2* a = A + (size_t)b * np * np + (size_t)src * np + k0 + c0;
   double2 v[4] = {a[0], a[1], a[2], a[3]};
   if (t == 0) bad = 0;
   auto publish = [&](int k, int buf) {
@@ -242,12 +246,13 @@ __global__ void __launch_bounds__(256) gj_pivot32_fp64_kernel(const double2* __r
   if (t == 0 && bad && status) atomicCAS(status, 0, DS_SINGULAR);
 }
 
-template <class T, int NB>
+// W columns of R and W rows of C per CTA (W = 8 for one matrix: 4 x more
+// CTAs than W = 32 on the same work).
+template <class T, int NB, int W = 32>
 __global__ void __launch_bounds__(256) gj_panels_kernel(const cplx_t<T>* __restrict__ A, int np, int k0,
                                                         const cplx_t<T>* __restrict__ Pbuf,
                                                         cplx_t<T>* __restrict__ Rbuf, cplx_t<T>* __restrict__ Cbuf) {
   using C = cplx_t<T>;
-  constexpr int W = 32;
   __shared__ C ps[NB][NB + 1];
   __shared__ C as[NB][W + 1];
   const int b = blockIdx.y;
@@ -284,18 +289,22 @@ __global__ void __launch_bounds__(256) gj_panels_kernel(const cplx_t<T>* __restr
   }
 }
 
-// 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs.
+// 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs; the
+// CTA columns start at tile jt0.  Column j is written iff (wlo <= j < whi) ==
+// inside: (0, 0, false) writes every column, (lo, hi, true) only the window
+// (the next step's panel, updated first), (lo, hi, false) all but the window.
 template <class T, int NB>
 __global__ void __launch_bounds__(256) gj_update_kernel(cplx_t<T>* __restrict__ A, int np, int k0,
                                                         const cplx_t<T>* __restrict__ Rbuf,
-                                                        const cplx_t<T>* __restrict__ Cbuf) {
+                                                        const cplx_t<T>* __restrict__ Cbuf, int jt0, int wlo,
+                                                        int whi, bool inside) {
   using C = cplx_t<T>;
   constexpr int TM = 64, TN = 64;
   extern __shared__ __align__(16) unsigned char smraw[];
   C (*cs)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smraw);
   C (*rs)[TN] = reinterpret_cast<C (*)[TN]>(smraw + sizeof(C) * TM * (NB + 1));
   const int b = blockIdx.z;
-  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  const int i0 = blockIdx.y * TM, j0 = (jt0 + blockIdx.x) * TN;
   const C* Cb = Cbuf + (size_t)b * np * NB;
   const C* R = Rbuf + (size_t)b * NB * np;
   for (int e = threadIdx.x; e < TM * NB; e += blockDim.x) cs[e / NB][e % NB] = Cb[(size_t)(i0 + e / NB) * NB + e % NB];
@@ -327,10 +336,43 @@ __global__ void __launch_bounds__(256) gj_update_kernel(cplx_t<T>* __restrict__ 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int j = j0 + tx + 16 * q;
+      if ((j >= wlo && j < whi) != inside) continue;
       bool jk = (j >= k0 && j < k0 + NB);
       C old = (ik || jk) ? mk<T>(0, 0) : a[(size_t)i * np + j];
       a[(size_t)i * np + j] = csub(old, acc[r][q]);
     }
+  }
+}
+
+// The update of one 32-column window [w0, w0 + 32) (the next step's panel)
+// on every row, in 8-row slices: 8 x 32 outputs per CTA of 64 threads, so
+// the window's few flops spread over many SMs.
+template <int NB>
+__global__ void __launch_bounds__(64) gj_update_window_kernel(double2* __restrict__ A, int np, int k0, int w0,
+                                                              const double2* __restrict__ Rbuf,
+                                                              const double2* __restrict__ Cbuf) {
+  __shared__ double2 cs[8][NB + 1];
+  __shared__ double2 rs[NB][32];
+  const int i0 = blockIdx.x * 8, t = threadIdx.x;
+  for (int e = t; e < 8 * NB; e += 64) cs[e / NB][e % NB] = Cbuf[(size_t)(i0 + e / NB) * NB + e % NB];
+  for (int e = t; e < NB * 32; e += 64) rs[e / 32][e % 32] = Rbuf[(size_t)(e / 32) * np + w0 + e % 32];
+  __syncthreads();
+  const int r = t >> 3, c0 = 4 * (t & 7);
+  double2 acc[4] = {};
+#pragma unroll 8
+  for (int kk = 0; kk < NB; ++kk) {
+    const double2 a = cs[r][kk];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma(acc[u], a, rs[kk][c0 + u]);
+  }
+  const int i = i0 + r;
+  const bool ik = i >= k0 && i < k0 + NB;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = w0 + c0 + u;
+    const bool jk = j >= k0 && j < k0 + NB;
+    double2* a = A + (size_t)i * np + j;
+    *a = csub((ik || jk) ? make_double2(0.0, 0.0) : *a, acc[u]);
   }
 }
 
@@ -343,12 +385,13 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
   NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int k0 = 0; k0 < np; k0 += NB) {
     static_assert(NB == 32, "the pivot-block kernel inverts 32 x 32 blocks");
-    gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, Pbuf, status);
+    gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, nullptr, Pbuf, status);
     NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
     gj_panels_kernel<T, NB><<<dim3(np / 32, nb_batch), 256, 0, st>>>(A, np, k0, Pbuf, Rbuf, Cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
     const int slot = instr_begin(st);
-    gj_update_kernel<T, NB><<<dim3(np / 64, np / 64, nb_batch), 256, smem, st>>>(A, np, k0, Rbuf, Cbuf);
+    gj_update_kernel<T, NB><<<dim3(np / 64, np / 64, nb_batch), 256, smem, st>>>(A, np, k0, Rbuf, Cbuf, 0, 0, 0,
+                                                                                 false);
     NED_LAUNCH_CHECK("gj_update_kernel");
     const int live = n - k0 < NB ? (n - k0 > 0 ? n - k0 : 0) : NB;
     instr_end(slot, st, 8.0 * (double)n * n * live * nb_batch,
@@ -377,11 +420,14 @@ constexpr int kTourNB = 32;
 // (rows k0 + i of the matrix when `in` is NULL, else in[i]; -1 = no row) and
 // writes the <= 32 rows it pivots on (in pivot order, -1 padded) to
 // out[c*32 ..].  With final != 0 (one block) it turns the winners into the
-// swap sequence piv[k0 .. k0+31] (position k0 + j swaps with piv[k0 + j]).
+// swap sequence piv[k0 .. k0+31] (position k0 + j swaps with piv[k0 + j]),
+// and the same swaps as one gather of the <= 64 rows they move: gather[0] =
+// count, then pairs (position, row now at that position before the swaps).
 __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restrict__ A, int np, int n, int k0,
                                                          const int* __restrict__ in, int in_count,
                                                          int* __restrict__ out, int final_round,
-                                                         int* __restrict__ piv, int* status) {
+                                                         int* __restrict__ piv, int* __restrict__ gather,
+                                                         int* status) {
   extern __shared__ float2 tp[];  // kTourRows x (kTourNB + 1)
   __shared__ int gidx[kTourRows];
   constexpr int LD = kTourNB + 1;
@@ -502,19 +548,34 @@ __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restri
         set_at(target, ra);
       }
     }
+    if (gather) {
+      int cnt = 0;
+      for (int u = 0; u < used; ++u)
+        if (pos_row[u] != pos_key[u]) {
+          gather[1 + 2 * cnt] = pos_key[u];
+          gather[2 + 2 * cnt] = pos_row[u];
+          ++cnt;
+        }
+      gather[0] = cnt;
+    }
   }
 }
 
-// Rows k0 + j <-> piv[k0 + j], j = 0 .. 31 in order; one thread per column.
-__global__ void apply_swaps_kernel(double2* __restrict__ A, int np, int n, int k0, const int* __restrict__ piv) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= np) return;
-  for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
-    const int p = piv[k0 + j];
-    if (p == k0 + j) continue;
-    const double2 a = A[(size_t)(k0 + j) * np + col];
-    A[(size_t)(k0 + j) * np + col] = A[(size_t)p * np + col];
-    A[(size_t)p * np + col] = a;
+// The swaps of one step as a gather: 32 columns per CTA, the moved rows'
+// values staged in shared memory, then written to their new positions.
+__global__ void __launch_bounds__(256) apply_gather_kernel(double2* __restrict__ A, int np,
+                                                           const int* __restrict__ gather) {
+  __shared__ double2 buf[2 * kTourNB][32];
+  const int cnt = gather[0];
+  const int col0 = blockIdx.x * 32;
+  for (int e = threadIdx.x; e < cnt * 32; e += blockDim.x) {
+    const int u = e >> 5, c = e & 31;
+    buf[u][c] = A[(size_t)gather[2 + 2 * u] * np + col0 + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < cnt * 32; e += blockDim.x) {
+    const int u = e >> 5, c = e & 31;
+    A[(size_t)gather[1 + 2 * u] * np + col0 + c] = buf[u][c];
   }
 }
 
@@ -553,9 +614,40 @@ size_t pivot_inverse_workspace(int n) {
   const int nchunk = (n + kTourRows - 1) / kTourRows;
   return align256(sizeof(double2) * (size_t)np * np) + align256(sizeof(double2) * kTourNB * kTourNB) +
          2 * align256(sizeof(double2) * (size_t)kTourNB * np) + 2 * align256(sizeof(int) * (size_t)nchunk * kTourNB) +
-         2 * align256(sizeof(int) * (size_t)n);
+         2 * align256(sizeof(int) * (size_t)n) + align256(sizeof(int) * (1 + 4 * kTourNB));
 }
 
+// Second stream (highest priority) and two events per device and host
+// thread for the look-ahead below, created on first use and kept.
+struct LookAhead {
+  cudaStream_t side = nullptr;
+  cudaEvent_t panel = nullptr, chain = nullptr;
+};
+
+int look_ahead(LookAhead** out) {
+  constexpr int kMaxDev = 64;
+  thread_local LookAhead la[kMaxDev];
+  int dev = 0;
+  NED_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return set_error(NEDMFT_ECUDA, "pivot_inverse: device %d out of range", dev);
+  LookAhead& l = la[dev];
+  if (!l.side) {
+    int lo = 0, hi = 0;
+    NED_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    NED_CUDA(cudaEventCreateWithFlags(&l.panel, cudaEventDisableTiming));
+    NED_CUDA(cudaEventCreateWithFlags(&l.chain, cudaEventDisableTiming));
+    NED_CUDA(cudaStreamCreateWithPriority(&l.side, cudaStreamNonBlocking, hi));
+  }
+  *out = &l;
+  return NEDMFT_OK;
+}
+
+// Every step's pivot choice (the tournament) and pivot-block inverse depend
+// only on the step's 32 panel columns, so they run one step ahead, on the
+// second stream: there step k updates the next step's panel columns, then
+// the tournament and the 32 x 32 inverse of step k + 1 run, while step k
+// updates the rest of the matrix on the caller's stream.  The swaps of step
+// k + 1 wait for both.
 int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   constexpr int NB = kTourNB;
   const int np = ((n + 63) / 64) * 64;
@@ -569,7 +661,11 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   cand[0] = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)nchunk * NB);
   cand[1] = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)nchunk * NB);
   int* piv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
-  int* inv = reinterpret_cast<int*>(p);
+  int* inv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
+  int* gather = reinterpret_cast<int*>(p);
+  LookAhead* la = nullptr;
+  int rc = look_ahead(&la);
+  if (rc) return rc;
   const size_t total = (size_t)np * np;
   int bx = (int)((total + 255) / 256);
   if (bx > 152 * 8) bx = 152 * 8;
@@ -577,33 +673,55 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   NED_LAUNCH_CHECK("pad_identity_kernel");
   const size_t upd_smem = sizeof(double2) * (64 * (NB + 1) + NB * 64);
   const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
-  {
-    int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<double, NB>), (int)upd_smem);
-    if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem);
-    if (rc) return rc;
-  }
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    // tournament rounds over the rows k0 .. n-1
+  rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<double, NB>), (int)upd_smem);
+  if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem);
+  if (rc) return rc;
+  // tournament over the rows k0 .. n-1 on the panel columns k0 .. k0+31, then
+  // the inverse of the winners' 32 x 32 block (read in their rows, before the
+  // swaps), on stream s
+  auto chain = [&](int k0, cudaStream_t s) -> int {
     const int* in = nullptr;
     int count = n - k0, buf = 0;
     while (true) {
       const int blocks = (count + kTourRows - 1) / kTourRows;
       const int fin = blocks == 1;
-      tour_kernel<<<blocks, kTourRows, tour_smem, st>>>(ap, np, n, k0, in, count, cand[buf], fin, piv, status);
+      tour_kernel<<<blocks, kTourRows, tour_smem, s>>>(ap, np, n, k0, in, count, cand[buf], fin, piv, gather,
+                                                       status);
       NED_LAUNCH_CHECK("tour_kernel");
       if (fin) break;
       in = cand[buf];
       count = blocks * kTourNB;
       buf ^= 1;
     }
-    apply_swaps_kernel<<<(np + 255) / 256, 256, 0, st>>>(ap, np, n, k0, piv);
-    NED_LAUNCH_CHECK("apply_swaps_kernel");
-    gj_pivot32_fp64_kernel<<<1, 256, 0, st>>>(ap, np, k0, pbuf, status);
+    gj_pivot32_fp64_kernel<<<1, 256, 0, s>>>(ap, np, k0, cand[buf], pbuf, status);
     NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
-    gj_panels_kernel<double, NB><<<dim3(np / 32, 1), 256, 0, st>>>(ap, np, k0, pbuf, rbuf, cbuf);
+    return NEDMFT_OK;
+  };
+  if ((rc = chain(0, st))) return rc;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    apply_gather_kernel<<<np / 32, 256, 0, st>>>(ap, np, gather);
+    NED_LAUNCH_CHECK("apply_gather_kernel");
+    gj_panels_kernel<double, NB, 8><<<dim3(np / 8, 1), 256, 0, st>>>(ap, np, k0, pbuf, rbuf, cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
-    gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf);
+    const int k1 = k0 + NB;  // the next step
+    if (k1 >= n) {
+      gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, 0, 0,
+                                                                                    false);
+      NED_LAUNCH_CHECK("gj_update_kernel");
+      break;
+    }
+    // side stream: this step's update of the next panel's columns, then the
+    // next step's tournament and pivot block; here: the rest of the update
+    NED_CUDA(cudaEventRecord(la->panel, st));
+    NED_CUDA(cudaStreamWaitEvent(la->side, la->panel, 0));
+    gj_update_window_kernel<NB><<<np / 8, 64, 0, la->side>>>(ap, np, k0, k1, rbuf, cbuf);
+    NED_LAUNCH_CHECK("gj_update_window_kernel");
+    if ((rc = chain(k1, la->side))) return rc;
+    NED_CUDA(cudaEventRecord(la->chain, la->side));
+    gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, k1,
+                                                                                  k1 + NB, false);
     NED_LAUNCH_CHECK("gj_update_kernel");
+    NED_CUDA(cudaStreamWaitEvent(st, la->chain, 0));
   }
   swap_colmap_kernel<<<1, 1, 0, st>>>(n, piv, inv);
   NED_LAUNCH_CHECK("swap_colmap_kernel");

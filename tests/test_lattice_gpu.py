@@ -210,11 +210,12 @@ def test_impurity_update_matches_oracle():
     assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
 
 
-@pytest.mark.parametrize("args", [(-2, 4, 0.2, 10, 0.5), (-2, 3, 0.05, 5.0, 0.25)])
+@pytest.mark.parametrize("args", [(-2, 4, 0.2, 10, 0.5), (-2, 3, 0.05, 5.0, 0.25), (-2, 4, 0.02, 10, 0.5)])
 def test_impurity_update_needs_pivoting(args):
     # G_loc = (cyclic row shift)(I + 0.3 R) with its diagonal set to zero:
     # every pivot of an elimination without row exchanges is 0 at the first
-    # step, so the inversions need them; N_c = 80 and 220 (ragged last blocks)
+    # step, so the inversions need them; N_c = 80, 220 and 620 (ragged last
+    # blocks; 620 rows take two tournament rounds per step)
     c = O.contour_grid(*args)
     g = api.contour_grid(*args)
     n = c.n_c
