@@ -647,7 +647,7 @@ def main():
     lat_step_ms = lat_ms / args.steps
     imp_step_ms = imp_ms / args.steps
     flops_lattice = 8.0 * n ** 3 * nq            # B-form: one complex inversion per point
-    flops_impurity = 4 * 8.0 * n ** 3            # four complex inversions
+    flops_impurity = 2 * 8.0 * n ** 3            # two complex inversions
     kern_tflops = (tfl.value / (tms.value / 1e3) / 1e12) if tms.value > 0 else 0.0
     kern_gbs = (tby.value / (tms.value / 1e3) / 1e9) if tms.value > 0 else 0.0
 
@@ -703,13 +703,13 @@ def main():
                 "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
                 "config": {"workload": W["name"], "n_c": n, "points": nq, "precision": prec,
                            "step": "one DMFT iteration: lattice step (B_q - S build, 2809 Dyson solves, FP64 "
-                                   "G_loc and j(t) sums) + impurity step (4 FP64 inversions)",
+                                   "G_loc and j(t) sums) + impurity step (2 FP64 inversions)",
                            "parallelism": f"dp{world} (one independent run per GPU)",
                            "l2": "inputs larger than L2 (every step streams >1 GB)"},
                 "lattice_ms": lat_step_ms, "impurity_ms": imp_step_ms, "lattice_steps_per_s": 1e3 / lat_step_ms,
                 "tflops": (flops_lattice + flops_impurity) / (ms_per_step / 1e3) / 1e12,
                 "tflops_lattice": flops_lattice / (lat_step_ms / 1e3) / 1e12,
-                "tflops_basis": "B-form 8 N_c^3 per solve; impurity 4 x 8 N_c^3",
+                "tflops_basis": "B-form 8 N_c^3 per solve; impurity 2 x 8 N_c^3 (two inversions)",
                 "solves_per_s": nq / (lat_step_ms / 1e3),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches.value),
                 "clocks": clk, "tts": tts}

@@ -289,57 +289,91 @@ __global__ void __launch_bounds__(256) gj_panels_kernel(const cplx_t<T>* __restr
   }
 }
 
-// 64 x 64 output tile per CTA, 256 threads, each 4 x 4 complex outputs; the
-// CTA columns start at tile jt0.  Column j is written iff (wlo <= j < whi) ==
-// inside: (0, 0, false) writes every column, (lo, hi, true) only the window
-// (the next step's panel, updated first), (lo, hi, false) all but the window.
-template <class T, int NB>
-__global__ void __launch_bounds__(256) gj_update_kernel(cplx_t<T>* __restrict__ A, int np, int k0,
-                                                        const cplx_t<T>* __restrict__ Rbuf,
-                                                        const cplx_t<T>* __restrict__ Cbuf, int jt0, int wlo,
-                                                        int whi, bool inside) {
-  using C = cplx_t<T>;
-  constexpr int TM = 64, TN = 64;
+// 64 x 64 output tile per CTA; each thread 4 rows x kUpdRN columns.  The
+// complex products use three real products (the 3M form): for a = ax + i ay,
+// b = bx + i by,  Re(ab) = ax bx - ay by  and  Im(ab) = (ax + ay)(bx + by) -
+// ax bx - ay by.  The three real sums over the 32 k run apart and combine at
+// the end: 3 FMAs per complex multiply-add instead of 4.  The sums ax + ay of
+// the C panel and bx + by of the R panel are formed once, in shared memory.
+// The CTA columns start at tile jt0.  Column j is written iff (wlo <= j <
+// whi) == inside: (0, 0, false) writes every column, (lo, hi, false) all but
+// a window that another kernel updates.
+constexpr int kUpdRN = 4;
+constexpr int kUpdThreads = 16 * (64 / kUpdRN);
+template <int NB>
+constexpr size_t upd_smem_bytes() {  // C panel and R panel tiles with their x + y sums
+  return (size_t)64 * (NB + 1) * 24 + (size_t)NB * 64 * 24;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kUpdThreads, 1) gj_update_kernel(double2* __restrict__ A, int np, int k0,
+                                                                   const double2* __restrict__ Rbuf,
+                                                                   const double2* __restrict__ Cbuf, int jt0,
+                                                                   int wlo, int whi, bool inside) {
+  constexpr int TM = 64, TN = 64, RN = kUpdRN, CX = TN / RN;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C (*cs)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smraw);
-  C (*rs)[TN] = reinterpret_cast<C (*)[TN]>(smraw + sizeof(C) * TM * (NB + 1));
+  double2 (*cz)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smraw);
+  double2 (*rz)[TN] = reinterpret_cast<double2 (*)[TN]>(smraw + sizeof(double2) * TM * (NB + 1));
+  double (*csum)[NB + 1] =
+      reinterpret_cast<double (*)[NB + 1]>(smraw + sizeof(double2) * (TM * (NB + 1) + NB * TN));
+  double (*rsum)[TN] = reinterpret_cast<double (*)[TN]>(smraw + sizeof(double2) * (TM * (NB + 1) + NB * TN) +
+                                                        sizeof(double) * TM * (NB + 1));
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * TM, j0 = (jt0 + blockIdx.x) * TN;
-  const C* Cb = Cbuf + (size_t)b * np * NB;
-  const C* R = Rbuf + (size_t)b * NB * np;
-  for (int e = threadIdx.x; e < TM * NB; e += blockDim.x) cs[e / NB][e % NB] = Cb[(size_t)(i0 + e / NB) * NB + e % NB];
-  for (int e = threadIdx.x; e < NB * TN; e += blockDim.x) rs[e / TN][e % TN] = R[(size_t)(e / TN) * np + j0 + e % TN];
+  const double2* Cb = Cbuf + (size_t)b * np * NB;
+  const double2* R = Rbuf + (size_t)b * NB * np;
+  for (int e = threadIdx.x; e < TM * NB; e += kUpdThreads) {
+    const double2 v = Cb[(size_t)(i0 + e / NB) * NB + e % NB];
+    cz[e / NB][e % NB] = v;
+    csum[e / NB][e % NB] = v.x + v.y;
+  }
+  for (int e = threadIdx.x; e < NB * TN; e += kUpdThreads) {
+    const double2 v = R[(size_t)(e / TN) * np + j0 + e % TN];
+    rz[e / TN][e % TN] = v;
+    rsum[e / TN][e % TN] = v.x + v.y;
+  }
   __syncthreads();
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  C acc[4][4];
+  const int tx = threadIdx.x % CX, ty = threadIdx.x / CX;
+  double pp[4][RN], mm[4][RN], ss[4][RN];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = mk<T>(0, 0);
-#pragma unroll 4
+    for (int q = 0; q < RN; ++q) pp[r][q] = mm[r][q] = ss[r][q] = 0.0;
+#pragma unroll 2
   for (int kk = 0; kk < NB; ++kk) {
-    C av[4], bv[4];
+    double2 av[4], bv[RN];
+    double as[4], bs[RN];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) av[r] = cs[ty + 16 * r][kk];
+    for (int r = 0; r < 4; ++r) {
+      av[r] = cz[ty + 16 * r][kk];
+      as[r] = csum[ty + 16 * r][kk];
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) bv[q] = rs[kk][tx + 16 * q];
+    for (int q = 0; q < RN; ++q) {
+      bv[q] = rz[kk][tx + CX * q];
+      bs[q] = rsum[kk][tx + CX * q];
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cfma(acc[r][q], av[r], bv[q]);
+      for (int q = 0; q < RN; ++q) {
+        pp[r][q] = fma(av[r].x, bv[q].x, pp[r][q]);
+        mm[r][q] = fma(av[r].y, bv[q].y, mm[r][q]);
+        ss[r][q] = fma(as[r], bs[q], ss[r][q]);
+      }
   }
-  C* a = A + (size_t)b * np * np;
+  double2* a = A + (size_t)b * np * np;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    int i = i0 + ty + 16 * r;
-    bool ik = (i >= k0 && i < k0 + NB);
+    const int i = i0 + ty + 16 * r;
+    const bool ik = (i >= k0 && i < k0 + NB);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int j = j0 + tx + 16 * q;
+    for (int q = 0; q < RN; ++q) {
+      const int j = j0 + tx + CX * q;
       if ((j >= wlo && j < whi) != inside) continue;
-      bool jk = (j >= k0 && j < k0 + NB);
-      C old = (ik || jk) ? mk<T>(0, 0) : a[(size_t)i * np + j];
-      a[(size_t)i * np + j] = csub(old, acc[r][q]);
+      const bool jk = (j >= k0 && j < k0 + NB);
+      const double2 old = (ik || jk) ? make_double2(0.0, 0.0) : a[(size_t)i * np + j];
+      a[(size_t)i * np + j] = make_double2(old.x - (pp[r][q] - mm[r][q]), old.y - (ss[r][q] - pp[r][q] - mm[r][q]));
     }
   }
 }
@@ -381,8 +415,8 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
                     int* status, cudaStream_t st) {
   constexpr int NB = 32;
   if (np % 64 != 0) return set_error(NEDMFT_EINVAL, "gj_blocked_simt: np=%d not a multiple of 64", np);
-  const size_t smem = sizeof(cplx_t<T>) * (64 * (NB + 1) + NB * 64);
-  NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = upd_smem_bytes<NB>();
+  NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int k0 = 0; k0 < np; k0 += NB) {
     static_assert(NB == 32, "the pivot-block kernel inverts 32 x 32 blocks");
     gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, nullptr, Pbuf, status);
@@ -390,7 +424,7 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
     gj_panels_kernel<T, NB><<<dim3(np / 32, nb_batch), 256, 0, st>>>(A, np, k0, Pbuf, Rbuf, Cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
     const int slot = instr_begin(st);
-    gj_update_kernel<T, NB><<<dim3(np / 64, np / 64, nb_batch), 256, smem, st>>>(A, np, k0, Rbuf, Cbuf, 0, 0, 0,
+    gj_update_kernel<NB><<<dim3(np / 64, np / 64, nb_batch), kUpdThreads, smem, st>>>(A, np, k0, Rbuf, Cbuf, 0, 0, 0,
                                                                                  false);
     NED_LAUNCH_CHECK("gj_update_kernel");
     const int live = n - k0 < NB ? (n - k0 > 0 ? n - k0 : 0) : NB;
@@ -671,9 +705,9 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   if (bx > 152 * 8) bx = 152 * 8;
   pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np);
   NED_LAUNCH_CHECK("pad_identity_kernel");
-  const size_t upd_smem = sizeof(double2) * (64 * (NB + 1) + NB * 64);
+  const size_t upd_smem = upd_smem_bytes<NB>();
   const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
-  rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<double, NB>), (int)upd_smem);
+  rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<NB>), (int)upd_smem);
   if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem);
   if (rc) return rc;
   // tournament over the rows k0 .. n-1 on the panel columns k0 .. k0+31, then
@@ -705,7 +739,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     NED_LAUNCH_CHECK("gj_panels_kernel");
     const int k1 = k0 + NB;  // the next step
     if (k1 >= n) {
-      gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, 0, 0,
+      gj_update_kernel<NB><<<dim3(np / 64, np / 64, 1), kUpdThreads, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, 0, 0,
                                                                                     false);
       NED_LAUNCH_CHECK("gj_update_kernel");
       break;
@@ -718,7 +752,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     NED_LAUNCH_CHECK("gj_update_window_kernel");
     if ((rc = chain(k1, la->side))) return rc;
     NED_CUDA(cudaEventRecord(la->chain, la->side));
-    gj_update_kernel<double, NB><<<dim3(np / 64, np / 64, 1), 256, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, k1,
+    gj_update_kernel<NB><<<dim3(np / 64, np / 64, 1), kUpdThreads, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, k1,
                                                                                   k1 + NB, false);
     NED_LAUNCH_CHECK("gj_update_kernel");
     NED_CUDA(cudaStreamWaitEvent(st, la->chain, 0));
