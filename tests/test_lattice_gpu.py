@@ -210,12 +210,14 @@ def test_impurity_update_matches_oracle():
     assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
 
 
-@pytest.mark.parametrize("args", [(-2, 4, 0.2, 10, 0.5), (-2, 3, 0.05, 5.0, 0.25), (-2, 4, 0.02, 10, 0.5)])
+@pytest.mark.parametrize("args", [(-1, 1, 0.25, 2.0, 0.5), (-1, 1, 0.125, 2.0, 0.5), (-2, 4, 0.2, 10, 0.5),
+                                  (-2, 2, 0.1, 4.0, 0.25), (-2, 3, 0.05, 5.0, 0.25), (-2, 4, 0.02, 10, 0.5)])
 def test_impurity_update_needs_pivoting(args):
     # G_loc = (cyclic row shift)(I + 0.3 R) with its diagonal set to zero:
     # every pivot of an elimination without row exchanges is 0 at the first
-    # step, so the inversions need them; N_c = 80, 220 and 620 (ragged last
-    # blocks; 620 rows take two tournament rounds per step)
+    # step, so the inversions need them; N_c = 20 (one 32-column step), 36 (a
+    # four-column last step), 80, 96 (three full steps), 220 and
+    # 620 (ragged last blocks; 620 rows take two tournament rounds per step)
     c = O.contour_grid(*args)
     g = api.contour_grid(*args)
     n = c.n_c
