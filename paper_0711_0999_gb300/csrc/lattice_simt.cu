@@ -416,7 +416,7 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
   constexpr int NB = 32;
   if (np % 64 != 0) return set_error(NEDMFT_EINVAL, "gj_blocked_simt: np=%d not a multiple of 64", np);
   const size_t smem = upd_smem_bytes<NB>();
-  NED_CUDA(cudaFuncSetAttribute(gj_update_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<NB>), (int)smem)) return rc;
   for (int k0 = 0; k0 < np; k0 += NB) {
     static_assert(NB == 32, "the pivot-block kernel inverts 32 x 32 blocks");
     gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, nullptr, Pbuf, status);
