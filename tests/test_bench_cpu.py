@@ -85,3 +85,13 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] == cores and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_default_held_out_pairs_take_one_pair_on_each_side_of_the_mott_transition():
+    u_mott = 2 ** 0.5
+    pairs = bench.held_out_pairs(16)
+    ins, met = bench.default_held_out_pairs(u_mott)
+    assert ins[0] >= u_mott > met[0]
+    # the first of each kind in the seeded held-out list, whatever its outcome
+    assert ins == next(p for p in pairs if p[0] >= u_mott)
+    assert met == next(p for p in pairs if p[0] < u_mott)
