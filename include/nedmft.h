@@ -356,9 +356,13 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  * D inv(A_h) D, and D (one entry per row, -U W_j at (j, j-1), +U W_0 at
  * (0, N-1)) makes the last product a gather.  Inversions: blocked
  * Gauss-Jordan (32 columns per step) whose pivot rows a tournament of
- * partial-pivoting rounds on 256-row chunks chooses.  gimp_d may be NULL;
+ * partial-pivoting rounds on 256-row chunks chooses; each step's tournament
+ * and pivot block run one step ahead on a second, library-owned stream of
+ * the highest priority (one per device and host thread), forked from and
+ * joined back into `stream` with events.  gimp_d may be NULL;
  * if given, G_imp = inv(A0 - W sigma_new W) costs a third inversion.
- * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered. */
+ * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered with respect
+ * to `stream`. */
 int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
                            const nedmft_c128* gloc_d,
                            const nedmft_c128* sigma_d,
@@ -380,7 +384,9 @@ int nedmft_impurity_update(const nedmft_contour* c, const nedmft_model* m,
  * Network: 17 features -> 4 tanh layers of 256 -> 2 outputs (Re, Im of X).
  * Parameters: one FP32 array of nedmft_mlp_param_count() values, layer by
  * layer, each layer a row-major (in x out) weight block followed by its
- * out biases.  GEMM operands are rounded to bf16, sums are FP32.
+ * out biases.  The GEMMs run on the tensor cores: operands rounded to bf16,
+ * sums in FP32; the weight gradients add their K slices in a fixed order, so
+ * nedmft_mlp_grad is deterministic.
  * Features of the pair (t_a, t_b), chosen to carry over from short training
  * contours to longer ones: U/2.5, E/4, tanh(Re(t_a - t_b)/3), then for t_a
  * and t_b in turn (real part r, imaginary depth tau) tanh(max(r, 0)/3) (the
