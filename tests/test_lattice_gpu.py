@@ -238,6 +238,54 @@ def test_impurity_update_needs_pivoting(args):
     assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
 
 
+def test_impurity_update_from_two_host_threads_matches_sequential_calls():
+    # each host thread gets its own look-ahead stream: two threads calling the
+    # impurity step at once, each on its own stream, give bit for bit the
+    # results of the same calls made one after the other (N_c = 220: 7 steps)
+    import threading
+
+    args = (-2, 3, 0.05, 5.0, 0.25)
+    c = O.contour_grid(*args)
+    g = api.contour_grid(*args)
+    n = c.n_c
+    mc = api.make_model(1.0, 1.0)
+    inputs = []
+    for seed in (11, 12):
+        rng = np.random.default_rng(seed)
+        base = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+        gl = np.roll(base, 1, axis=0).astype(np.complex128)
+        np.fill_diagonal(gl, 0.0)
+        inputs.append((torch.as_tensor(gl, device="cuda"),
+                       torch.as_tensor(workload_sigma(c.t, c.w, 1.0, seed=seed), device="cuda")))
+    ref = [api.impurity_update(g, mc, gl, sig, want_gimp=True) for gl, sig in inputs]
+    torch.cuda.synchronize()
+    api.check_status()
+    out = [None, None]
+    errors = []
+    start = threading.Barrier(2)
+
+    def work(k):
+        try:
+            s = torch.cuda.Stream()
+            start.wait()
+            with torch.cuda.stream(s):
+                for _ in range(4):
+                    out[k] = api.impurity_update(g, mc, *inputs[k], want_gimp=True, stream=s)
+            s.synchronize()
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    api.check_status()
+    for k in range(2):
+        assert torch.equal(out[k][0], ref[k][0]) and torch.equal(out[k][1], ref[k][1])
+
+
 def test_dmft_solve_small_config_matches_oracle():
     args = (-2, 4, 0.2, 10, 0.5)
     c = O.contour_grid(*args)
