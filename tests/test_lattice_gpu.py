@@ -109,6 +109,23 @@ def test_lattice_wide_gauss_jordan_blocks(args, n_c):
     assert np.abs(ji - jref.imag).max() < tj
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("args,n_c", [((-2, 2, 0.25, 3.5, 0.5), 39), ((-2, 3, 0.05, 5.5, 0.5), 211),
+                                      ((-2, 4, 0.02, 10.5, 0.5), 621)])
+def test_lattice_odd_contour_sizes(prec, args, n_c):
+    # an odd number of thermal points makes N_c odd: rows of odd length in the
+    # FP64 small and blocked paths, and on the mixed path padded to 128, 256
+    # and 640 (128-column steps chosen by the padding rule)
+    c, g, mo, mc, sig, eps, ebar, wq = setup(args, 1.0, 1.5, 3, seed=13)
+    assert c.n_c == n_c
+    ref, jref = O.lattice_gloc(c, mo, sig, eps, ebar, wq)
+    gl, j, ji = run_gpu(g, mc, sig, eps, ebar, wq, prec)
+    tg, tj = TOL[prec]
+    assert rel(gl, ref) < tg
+    assert np.abs(j - jref.real).max() < tj
+    assert np.abs(ji - jref.imag).max() < tj
+
+
 def test_lattice_many_batches_fp64():
     # more points than one batch of the blocked FP64 path (152), N_c = 130
     c, g, mo, mc, sig, eps, ebar, wq = setup((-1, 2, 0.05, 1.0, 0.1), 1.0, 1.0, 13, seed=9)
@@ -211,12 +228,13 @@ def test_impurity_update_matches_oracle():
 
 
 @pytest.mark.parametrize("args", [(-1, 1, 0.25, 2.0, 0.5), (-1, 1, 0.125, 2.0, 0.5), (-2, 4, 0.2, 10, 0.5),
-                                  (-2, 2, 0.1, 4.0, 0.25), (-2, 3, 0.05, 5.0, 0.25), (-2, 4, 0.02, 10, 0.5)])
+                                  (-2, 2, 0.1, 4.0, 0.25), (-2, 3, 0.05, 5.0, 0.25), (-2, 3, 0.05, 5.5, 0.5),
+                                  (-2, 4, 0.02, 10, 0.5)])
 def test_impurity_update_needs_pivoting(args):
     # G_loc = (cyclic row shift)(I + 0.3 R) with its diagonal set to zero:
     # every pivot of an elimination without row exchanges is 0 at the first
     # step, so the inversions need them; N_c = 20 (one 32-column step), 36 (a
-    # four-column last step), 80, 96 (three full steps), 220 and
+    # four-column last step), 80, 96 (three full steps), 220, 211 (odd) and
     # 620 (ragged last blocks; 620 rows take two tournament rounds per step)
     c = O.contour_grid(*args)
     g = api.contour_grid(*args)
