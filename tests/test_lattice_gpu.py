@@ -126,6 +126,31 @@ def test_lattice_odd_contour_sizes(prec, args, n_c):
     assert np.abs(ji - jref.imag).max() < tj
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("args,n_c", [((0, 1, 1.0, 1.0, 1.0), 3), ((0, 1, 1.0, 2.0, 1.0), 4),
+                                      ((0, 2, 1.0, 4.0, 1.0), 8), ((-1, 2, 0.5, 0.5, 0.5), 13)])
+def test_tiny_contours(prec, args, n_c):
+    # the smallest contours (one real step, one thermal point, ...): the lattice
+    # step on both paths and the impurity step against the oracle
+    c, g, mo, mc, sig, eps, ebar, wq = setup(args, 1.0, 1.0, 4, seed=17)
+    assert c.n_c == n_c
+    ref, jref = O.lattice_gloc(c, mo, sig, eps, ebar, wq)
+    gl, j, ji = run_gpu(g, mc, sig, eps, ebar, wq, prec)
+    tg, tj = TOL[prec]
+    assert rel(gl, ref) < tg
+    assert np.abs(j - jref.real).max() < tj
+    assert np.abs(ji - jref.imag).max() < tj
+    if prec == "fp64":
+        s_ref, gi_ref = O.impurity_update(c, mo, ref, sig)
+        s_new, gimp = api.impurity_update(g, mc, torch.as_tensor(ref, device="cuda"),
+                                          torch.as_tensor(sig, device="cuda"), want_gimp=True)
+        torch.cuda.synchronize()
+        api.check_status()
+        sw = lambda s: c.w[:, None] * s * c.w[None, :]
+        assert rel(sw(s_new.cpu().numpy()), sw(s_ref)) < 1e-10
+        assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
+
+
 def test_lattice_many_batches_fp64():
     # more points than one batch of the blocked FP64 path (152), N_c = 130
     c, g, mo, mc, sig, eps, ebar, wq = setup((-1, 2, 0.05, 1.0, 0.1), 1.0, 1.0, 13, seed=9)
@@ -317,6 +342,24 @@ def test_dmft_solve_small_config_matches_oracle():
     w = c.w
     sw = lambda s: w[:, None] * s * w[None, :]
     assert rel(sw(sol.sigma.cpu().numpy()), sw(ref.sigma)) < 1e-8
+
+
+def test_largest_contour_of_the_paper_sampled_points():
+    # N_c = 5700, the paper's largest contour (t in [-5, 51], dt = 0.02, dtau =
+    # 0.1): 2 points of the 16 x 16 grid near its centre, weights renormalised;
+    # the mixed path pads to 5888 (23 steps of 256 columns)
+    args = (-5, 51, 0.02, 10.0, 0.1)
+    c, g, mo, mc, sig, _, _, _ = setup(args, 1.0, 1.0, 2, seed=23)
+    assert c.n_c == 5700
+    eps_all, ebar_all, wq_all = O.quadrature_points(16)
+    pick = [7 * 16 + 8, 8 * 16 + 6]
+    eps, ebar, wq = eps_all[pick], ebar_all[pick], wq_all[pick] / wq_all[pick].sum()
+    ref, jref = O.lattice_gloc(c, mo, sig, eps, ebar, wq)
+    for prec in ("mixed_bf16", "fp64"):
+        gl, j, _ = run_gpu(g, mc, sig, eps, ebar, wq, prec)
+        tg, tj = TOL[prec]
+        assert rel(gl, ref) < tg, prec
+        assert np.abs(j - jref.real).max() < tj, prec
 
 
 def test_long_contour_sampled_points():
