@@ -1,11 +1,15 @@
 // Tensor-core (tcgen05) path of the lattice step.
 //
 // Gauss-Jordan on A'_q (np x np, FP32 complex, batch of nb matrices) in
-// steps of 128 columns.  Step k0:
-//   gj_pivot_pack   P = inv(A_KK) in shared memory (FP32), packed bf16 hi/lo
+// steps of W = 128 or 256 columns.  Step k0:
+//   P = inv(A_KK)   W = 128: gj_pivot_pack, in shared memory (FP32); W = 256:
+//                   the 128-column Gauss-Jordan below on a copy of the
+//                   256 x 256 block (gj_extract), packed by gj_ppack; P is
+//                   packed bf16 hi/lo
 //   gj_panel_pack   C' = A_{:,K} (C'_K = -I) packed as the update's A operand;
 //                   A_{K,:}^T (A_KK -> I), 2x2 real-embedded, packed as the
-//                   R-product's B operand
+//                   R-product's B operand (first step only: later steps'
+//                   panels come from the update's epilogue)
 //   umma_gemm       R = P A_{K,:} (bf16x3), written packed as the update's B
 //   umma_gemm       A <- A (rows K, cols K zeroed) - C' R (bf16x3)
 // A complex product is a real GEMM on interleaved storage: the A operand is
@@ -1028,31 +1032,48 @@ __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __res
 }
 
 // Copy of the W x W diagonal block A_KK of every matrix (inverted in place by
-// the W = 128 Gauss-Jordan when the outer block is wider).
+// the W = 128 Gauss-Jordan when the outer block is wider).  Block (x, y): rows
+// 8x .. 8x+7 of matrix y, two entries (16 bytes) per thread and step.
+constexpr int kPackRows = 8;
 template <int W>
 __global__ void __launch_bounds__(256) gj_extract_kernel(const float2* __restrict__ A, int np, int k0,
                                                          float2* __restrict__ out) {
-  const int b = blockIdx.y, r = blockIdx.x;
-  const float2* src = A + (size_t)b * np * np + (size_t)(k0 + r) * np + k0;
-  float2* dst = out + ((size_t)b * W + r) * W;
-  for (int c = threadIdx.x; c < W; c += blockDim.x) dst[c] = src[c];
+  const int b = blockIdx.y, r0 = blockIdx.x * kPackRows;
+  for (int e = threadIdx.x; e < kPackRows * W / 2; e += blockDim.x) {
+    const int r = r0 + e / (W / 2), c = 2 * (e % (W / 2));
+    const float4 v = *reinterpret_cast<const float4*>(A + (size_t)b * np * np + (size_t)(k0 + r) * np + k0 + c);
+    *reinterpret_cast<float4*>(out + ((size_t)b * W + r) * W + c) = v;
+  }
 }
 
-// P = inv(A_KK) (W x W, FP32) as the R-product's A operand: row r, k = 2c / 2c+1.
+// P = inv(A_KK) (W x W, FP32) as the R-product's A operand: row r, k = 2c /
+// 2c+1.  Block (x, y): rows 8x .. 8x+7 of matrix y (one 8-row group); a
+// thread takes 4 consecutive entries, one 16-byte core-matrix row per slice,
+// and 8 consecutive threads the 8 rows of one 128-byte core matrix.
 template <int W>
 __global__ void __launch_bounds__(256) gj_ppack_kernel(const float2* __restrict__ Pinv, __nv_bfloat16* __restrict__ pimg,
                                                        size_t pstride, size_t pslice) {
-  const int b = blockIdx.y, r = blockIdx.x;
-  const float2* src = Pinv + ((size_t)b * W + r) * W;
+  static_assert(kPackRows == 8, "one core-matrix row group per block");
+  const int b = blockIdx.y, r0 = blockIdx.x * kPackRows;
   __nv_bfloat16* dst = pimg + b * pstride;
-  for (int c = threadIdx.x; c < W; c += blockDim.x) {
-    const float2 z = src[c];
-    __nv_bfloat16 rh, rl, ih, il;
-    split2(z.x, rh, rl);
-    split2(z.y, ih, il);
-    const size_t o = img_offset(r, 2 * c, 2 * W / kTileK);
-    *reinterpret_cast<__nv_bfloat162*>(dst + o) = __halves2bfloat162(rh, ih);
-    *reinterpret_cast<__nv_bfloat162*>(dst + pslice + o) = __halves2bfloat162(rl, il);
+  for (int e = threadIdx.x; e < kPackRows * W / 4; e += blockDim.x) {
+    const int r = r0 + (e & 7), c4 = 4 * (e >> 3);
+    const float4* src = reinterpret_cast<const float4*>(Pinv + ((size_t)b * W + r) * W + c4);
+    const float4 z01 = src[0], z23 = src[1];
+    const float2 z[4] = {make_float2(z01.x, z01.y), make_float2(z01.z, z01.w), make_float2(z23.x, z23.y),
+                         make_float2(z23.z, z23.w)};
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat16 rh, rl, ih, il;
+      split2(z[q].x, rh, rl);
+      split2(z[q].y, ih, il);
+      hi[q] = bf2_bits(rh, ih);
+      lo[q] = bf2_bits(rl, il);
+    }
+    const size_t o = img_offset(r, 2 * c4, 2 * W / kTileK);
+    *reinterpret_cast<uint4*>(dst + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(dst + pslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -1274,11 +1295,11 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
       char* inner = scratch + per * nb;
       float2* Xs = reinterpret_cast<float2*>(inner);
       char* inner_scratch = inner + gj_buffers<128>(W).mat * nb;
-      gj_extract_kernel<W><<<dim3(W, nb), 256, 0, st>>>(A, np, k0, Xs);
+      gj_extract_kernel<W><<<dim3(W / kPackRows, nb), 256, 0, st>>>(A, np, k0, Xs);
       NED_LAUNCH_CHECK("gj_extract_kernel");
       int rc = gj_blocked_umma_w<128>(Xs, W, W, nb, inner_scratch, status, st, false);
       if (rc) return rc;
-      gj_ppack_kernel<W><<<dim3(W, nb), 256, 0, st>>>(Xs, pimg, pstride, pslice);
+      gj_ppack_kernel<W><<<dim3(W / kPackRows, nb), 256, 0, st>>>(Xs, pimg, pstride, pslice);
       NED_LAUNCH_CHECK("gj_ppack_kernel");
     }
     {  // R = P A_{K,:}, W x 2np, K = 2W
@@ -1541,7 +1562,8 @@ __global__ void base_neg_s_kernel(ContourDev c, const double2* __restrict__ S, f
 // n = 2j, 2j+1; k = 2k', 2k'+1; [[re, -im], [im, re]] of X'[k'][j]) with a
 // power-of-two scale per column j, and X' hi/lo as the correction's A
 // operand.  Block (x, y): complex columns x*32 .. +31 of matrix y; tiles of
-// 32 x 32 pass through shared memory so both images are written along k.
+// 32 x 32 pass through shared memory, and both images are written in whole
+// 16-byte core-matrix rows.
 __global__ void __launch_bounds__(256) oz_pack_x_kernel(const float2* __restrict__ X, int np, int q0,
                                                         const int* __restrict__ flags, __nv_bfloat16* __restrict__ ximg,
                                                         int* __restrict__ xexp, __nv_bfloat16* __restrict__ aimg) {
@@ -1574,36 +1596,62 @@ __global__ void __launch_bounds__(256) oz_pack_x_kernel(const float2* __restrict
   }
   __syncthreads();
   for (int k0 = 0; k0 < np; k0 += 32) {
-    // coalesced load of rows k0 .. k0+31, columns j0 .. j0+31; the A image along j
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int k = k0 + rr, j = j0 + tx;
-      const float2 z = x[(size_t)k * np + j];
-      tile[rr][tx] = z;
-      __nv_bfloat16 rh, rl, ih, il;
-      split2(z.x, rh, rl);
-      split2(z.y, ih, il);
-      const size_t o = img_offset(k, 2 * j, kt);
-      *reinterpret_cast<__nv_bfloat162*>(ai + o) = __halves2bfloat162(rh, ih);
-      *reinterpret_cast<__nv_bfloat162*>(ai + as + o) = __halves2bfloat162(rl, il);
-    }
+    // coalesced load of rows k0 .. k0+31, columns j0 .. j0+31
+    for (int rr = ty; rr < 32; rr += 8) tile[rr][tx] = x[(size_t)(k0 + rr) * np + j0 + tx];
     __syncthreads();
-    // the B image along k: thread tx takes row k0 + tx of column j0 + cc
-    for (int cc = ty; cc < 32; cc += 8) {
-      const int j = j0 + cc, k = k0 + tx;
-      const float2 z = tile[tx][cc];
-      const int e = cexp[cc];
-      float r[2] = {ldexpf(z.x, -e), ldexpf(z.y, -e)};
-      const size_t o0 = img_offset(2 * j, 2 * k, kt), o1 = img_offset(2 * j + 1, 2 * k, kt);
+    {
+      // the A image (hi, lo): thread t writes one 16-byte core-matrix row,
+      // row k = k0 + 8 (t / 64) + t % 8 and entries j0 + 4 c .. +3, c = (t / 8) % 8,
+      // so 8 consecutive threads fill one 128-byte core matrix
+      const int t = threadIdx.x;
+      const int kr = 8 * (t >> 6) + (t & 7), c = (t >> 3) & 7;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 z = tile[kr][4 * c + q];
+        __nv_bfloat16 rh, rl, ih, il;
+        split2(z.x, rh, rl);
+        split2(z.y, ih, il);
+        hi[q] = bf2_bits(rh, ih);
+        lo[q] = bf2_bits(rl, il);
+      }
+      const size_t o = img_offset(k0 + kr, 2 * (j0 + 4 * c), kt);
+      *reinterpret_cast<uint4*>(ai + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(ai + as + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    {
+      // the B image: rows 2j, 2j+1 (j = j0 + 4 g + p, g = t / 32, p = t % 4) and
+      // k = k0 + 4 c .. +3 (c = (t / 4) % 8): two 16-byte core-matrix rows per
+      // slice, 4 consecutive threads fill one core matrix
+      const int t = threadIdx.x;
+      const int jl = 4 * (t >> 5) + (t & 3), c = (t >> 2) & 7;
+      const int j = j0 + jl;
+      const int e = cexp[jl];
+      float r[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 z = tile[4 * c + q][jl];
+        r[q][0] = ldexpf(z.x, -e);
+        r[q][1] = ldexpf(z.y, -e);
+      }
+      const size_t o0 = img_offset(2 * j, 2 * (k0 + 4 * c), kt), o1 = img_offset(2 * j + 1, 2 * (k0 + 4 * c), kt);
       for (int sl = 0; sl < kOzS; ++sl) {
-        float q[2];
-        for (int t = 0; t < 2; ++t) {
-          q[t] = rintf(ldexpf(r[t], kOzBits));
-          r[t] = ldexpf(r[t], kOzBits) - q[t];
+        uint32_t ev[4], od[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float qv[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            qv[u] = rintf(ldexpf(r[q][u], kOzBits));
+            r[q][u] = ldexpf(r[q][u], kOzBits) - qv[u];
+          }
+          const __nv_bfloat16 re = __float2bfloat16_rn(qv[0]), im = __float2bfloat16_rn(qv[1]);
+          const __nv_bfloat16 nim = __float2bfloat16_rn(-qv[1]);
+          ev[q] = bf2_bits(re, nim);  // row 2j: [re, -im]
+          od[q] = bf2_bits(im, re);   // row 2j+1: [im, re]
         }
-        const __nv_bfloat16 re = __float2bfloat16_rn(q[0]), im = __float2bfloat16_rn(q[1]);
-        const __nv_bfloat16 nim = __float2bfloat16_rn(-q[1]);
-        *reinterpret_cast<__nv_bfloat162*>(xi + sl * xs + o0) = __halves2bfloat162(re, nim);
-        *reinterpret_cast<__nv_bfloat162*>(xi + sl * xs + o1) = __halves2bfloat162(im, re);
+        *reinterpret_cast<uint4*>(xi + sl * xs + o0) = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+        *reinterpret_cast<uint4*>(xi + sl * xs + o1) = make_uint4(od[0], od[1], od[2], od[3]);
       }
     }
     __syncthreads();
