@@ -178,6 +178,7 @@ extern "C" int nedmft_dmft_solve(const nedmft_contour* c, const nedmft_model* m,
   if (rc) return rc;
   int cur = 0;  // s[cur], g[cur] hold the latest pair
   if (max_iter > 1) {
+    if ((rc = pivot_inverse_prepare())) return rc;  // no stream creation or attribute change inside the capture
     for (int par = 0; par < 2; ++par) {
       NED_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       int crc = nedmft_impurity_update(c, m, reinterpret_cast<const nedmft_c128*>(g[par]),

@@ -31,5 +31,6 @@ int launch_finish_current(int nt, const double2* jacc, double* j, double* ji, cu
 // Dense FP64 inversion with partial pivoting (impurity step).
 size_t pivot_inverse_workspace(int n);
 int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status);
+int pivot_inverse_prepare();  // before capturing pivot_inverse into a graph
 
 }  // namespace nedmft

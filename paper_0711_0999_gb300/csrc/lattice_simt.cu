@@ -676,6 +676,18 @@ int look_ahead(LookAhead** out) {
   return NEDMFT_OK;
 }
 
+// Creates this host thread's look-ahead stream and events on the current
+// device and sets the kernels' shared-memory limits: for callers that are
+// about to capture pivot_inverse into a CUDA graph.
+int pivot_inverse_prepare() {
+  LookAhead* la = nullptr;
+  int rc = look_ahead(&la);
+  if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<kTourNB>), (int)upd_smem_bytes<kTourNB>());
+  if (!rc)
+    rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)(sizeof(float2) * kTourRows * (kTourNB + 1)));
+  return rc;
+}
+
 // Every step's pivot choice (the tournament) and pivot-block inverse depend
 // only on the step's 32 panel columns, so they run one step ahead, on the
 // second stream: there step k updates the next step's panel columns, then

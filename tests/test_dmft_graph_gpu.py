@@ -69,3 +69,31 @@ def test_graph_loop_single_iteration():
     gl, _, _ = api.lattice_gloc(g, m, torch.zeros_like(sol.sigma), eps, ebar, wq, precision="fp64")
     torch.cuda.synchronize()
     assert float((sol.gloc - gl).abs().max()) < 1e-14
+
+
+def test_graph_loop_from_a_fresh_host_thread():
+    # a host thread that has never run an impurity step captures the loop
+    # (its look-ahead stream is made before the capture): the same result as
+    # on the main thread, bit for bit
+    import threading
+
+    g = api.contour_grid(-2, 4, 0.2, 10, 0.5)
+    m = api.make_model(0.5, 1.0)
+    ref = api.dmft_solve(g, m, 8, "fp64", tol=1e-8, max_iter=40)
+    torch.cuda.synchronize()
+    out, errors = [], []
+
+    def work():
+        try:
+            out.append(api.dmft_solve(g, m, 8, "fp64", tol=1e-8, max_iter=40))
+            torch.cuda.synchronize()
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    assert not errors, errors
+    sol = out[0]
+    assert sol.converged and sol.iterations == ref.iterations
+    assert torch.equal(sol.gloc, ref.gloc) and torch.equal(sol.sigma, ref.sigma)
