@@ -358,8 +358,10 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  * Gauss-Jordan (32 columns per step) whose pivot rows a tournament of
  * partial-pivoting rounds on 256-row chunks chooses; each step's tournament
  * and pivot block run one step ahead on a second, library-owned stream of
- * the highest priority (one per device and host thread), forked from and
- * joined back into `stream` with events.  gimp_d may be NULL;
+ * the highest priority (one per device and host thread, made by the thread's
+ * first call), forked from and joined back into `stream` with events; to
+ * capture the call into a CUDA graph, call it once outside the capture first
+ * (nedmft_dmft_solve does so for its own graph).  gimp_d may be NULL;
  * if given, G_imp = inv(A0 - W sigma_new W) costs a third inversion.
  * sigma_new_d may not alias gloc_d or sigma_d.  Stream-ordered with respect
  * to `stream`. */
