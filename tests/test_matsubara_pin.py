@@ -20,7 +20,9 @@ lattice or impurity step would leave an O(1) difference instead.
 
 The same first-order structure shows in the field dependence: in the exact
 theory the thermal block does not depend on E (causality), on the discrete
-contour it does at O(dt E^2), and that difference halves with dt.
+contour it does at O(dt E^2), and that difference halves with dt.  Likewise
+the Keldysh symmetry G^<(t, t')^* = -G^<(t', t) of the interacting G_loc, and
+its time-translation invariance at E = 0, hold to first order in the step.
 """
 
 import numpy as np
@@ -115,3 +117,26 @@ def test_field_dependence_of_the_thermal_block_is_first_order_in_dt():
     assert diffs[2] < 5e-4
     for a, b in zip(diffs, diffs[1:]):
         assert 0.4 < b / a < 0.7
+
+
+@pytest.mark.parametrize("E", [0.0, 1.0])
+def test_keldysh_symmetry_and_time_translation_are_first_order(E):
+    # the interacting G_loc keeps G^<(t, t')^* = -G^<(t', t) (and, at E = 0,
+    # depends on t - t' only) in the continuum; on the discrete contour both
+    # hold to first order in dt = dtau, so the violation halves with the step
+    sym, tti = [], []
+    for d in (0.2, 0.1, 0.05):
+        c = O.contour_grid(-1.0, 1.0, d, BETA, d)
+        r = O.dmft_solve(c, O.Model(U=U, E=E), n_quad=8, tol=1e-11, max_iter=80)
+        assert r.converged
+        g, nt = r.gloc, c.n_t
+        lo = lambda m: 2 * nt - m if m > 0 else 2 * nt  # the lower-branch (or first thermal) partner of t_m
+        sym.append(max(abs(np.conj(g[m, lo(k)]) + g[k, lo(m)]) for m in range(nt) for k in range(nt)))
+        tti.append(max(abs(g[m, lo(k)] - g[m - 1, lo(k - 1)]) for m in range(1, nt) for k in range(1, nt)))
+    for a, b in zip(sym, sym[1:]):
+        assert 0.35 < b / a < 0.6
+    assert sym[-1] < 0.05
+    if E == 0.0:
+        for a, b in zip(tti, tti[1:]):
+            assert 0.3 < b / a < 0.6
+        assert tti[-1] < 0.02
