@@ -248,10 +248,8 @@ def load_peaks():
 # DRAM bytes of one Gauss-Jordan update launch (152 matrices at N_c = 1500) from
 # an ncu capture of the kernel as it stands; None while the kernel has changed
 # since the counters were taken
-UPDATE_TRAFFIC_BYTES = 7.12e9
-UPDATE_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 16 matrices "
-                       "(431.7 + 317.9 MB), scaled by 152/16 to the 152-matrix launch; 1.24x the "
-                       "algorithmic 2 x N_c^2 x 8 B per matrix: the rest is the C' and R operand panels")
+UPDATE_TRAFFIC_BYTES = None
+UPDATE_TRAFFIC_NOTE = None
 
 
 def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str):

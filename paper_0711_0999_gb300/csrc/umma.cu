@@ -70,18 +70,41 @@ struct Cfg {
   static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
 };
 
-// bf16x3: hi*hi + hi*lo + lo*hi, one accumulator.
+// bf16x3: hi*hi + hi*lo + lo*hi, one accumulator.  A pair list names the
+// A and B slices of each product, the accumulator it adds into (kAccs
+// accumulators of kBn columns per tile) and whether it is the first product
+// of that accumulator in a K step.
 struct Split3 {
   static constexpr int kPairs = 3;
+  static constexpr int kAccs = 1;
   __device__ static int a(int p) { return p == 2 ? 1 : 0; }
   __device__ static int b(int p) { return p == 1 ? 1 : 0; }
+  __device__ static int acc(int) { return 0; }
+  __device__ static bool first(int p) { return p == 0; }
 };
 
 // hi*hi alone: for a product whose own rounding lies far below the target.
 struct Split1 {
   static constexpr int kPairs = 1;
+  static constexpr int kAccs = 1;
   __device__ static int a(int) { return 0; }
   __device__ static int b(int) { return 0; }
+  __device__ static int acc(int) { return 0; }
+  __device__ static bool first(int) { return true; }
+};
+
+// Two bf16x3 products into two accumulators: A slices (hi, lo) of variant 0
+// then of variant 1, one B (hi, lo); accumulator v takes A variant v times B.
+// The R product uses it with A = P' = (Re P, -Im P) and P'' = (Im P, Re P)
+// row-interleaved over k, and B = A_{K,:} as (Re, Im) pairs over k: the two
+// accumulators are Re R and Im R.
+struct Split3x2 {
+  static constexpr int kPairs = 6;
+  static constexpr int kAccs = 2;
+  __device__ static int a(int p) { return 2 * (p / 3) + (p % 3 == 2 ? 1 : 0); }
+  __device__ static int b(int p) { return p % 3 == 1 ? 1 : 0; }
+  __device__ static int acc(int p) { return p / 3; }
+  __device__ static bool first(int p) { return p % 3 == 0; }
 };
 
 template <class C, class Pairs, class Epi>
@@ -220,6 +243,9 @@ struct CfgHalf {
   static constexpr int kRedBuf = 2;  // staging boxes per epilogue warp
 };
 using CfgGJH = CfgHalf<256, 2, 2, 4>;
+// The R product: 128 complex columns per tile, A slices P' and P'' (hi, lo),
+// B (hi, lo) of A_{K,:}; two accumulators (Re R, Im R) of 128 columns each.
+using CfgRP = CfgHalf<128, 4, 2, 4>;
 
 // The same operands for a CTA pair, whose CTAs hold half of B each: stages of
 // 32 KB instead of 48 KB.  The update (N_c = 1500) ran fastest with the freed
@@ -284,7 +310,8 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
   const int G = gridDim.x / PAIR;
   const int cta = blockIdx.x / PAIR;
   const int rank = PAIR == 2 ? (int)cluster_ctarank() : 0;
-  constexpr uint32_t kCols = 2 * C::kBn;  // two accumulators
+  constexpr uint32_t kAccCols = C::kBn * Pairs::kAccs;  // one tile's accumulators
+  constexpr uint32_t kCols = 2 * kAccCols;                // two tiles in flight
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -369,7 +396,7 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
           if (!mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
         }
-        const uint32_t d = tmem + buf * C::kBn;
+        const uint32_t d = tmem + buf * kAccCols;
         for (int h = 0; h < 2 * p.kt; ++h, ++it) {
           const int s = it % C::kStages;
           if (!mbar_wait(&full[s], (it / C::kStages) & 1, abort_flag)) { ok = false; break; }
@@ -382,11 +409,12 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
             for (int q = 0; q < Pairs::kPairs; ++q) {
               const uint32_t a_addr = st + Pairs::a(q) * C::kHalfBytes + kk * 256;
               const uint32_t b_addr = st + (C::kSa + Pairs::b(q) * kBPer) * C::kHalfBytes + kk * 256;
-              const uint32_t acc = (h > 0 || kk > 0 || q > 0) ? 1u : 0u;
+              const uint32_t acc = (h > 0 || kk > 0 || !Pairs::first(q)) ? 1u : 0u;
+              const uint32_t dq = d + Pairs::acc(q) * C::kBn;
               if constexpr (PAIR == 2)
-                mma_bf16_pair(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
+                mma_bf16_pair(dq, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
               else
-                mma_bf16(d, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
+                mma_bf16(dq, smem_desc(a_addr, 128, 512), smem_desc(b_addr, 128, 512), idesc, acc);
             }
           }
           if constexpr (PAIR == 2) {
@@ -460,8 +488,12 @@ __global__ void __launch_bounds__(64 + 32 * EPIW, 1)
 #pragma unroll 1
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * C::kBn + c0, v);
-        if constexpr (Epi::kStage) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * kAccCols + c0, v);
+        if constexpr (Pairs::kAccs == 2) {
+          float v2[32];  // the same columns of the second accumulator
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * kAccCols + C::kBn + c0, v2);
+          epi(b, mt, nt, row, c0, v, v2);
+        } else if constexpr (Epi::kStage) {
           const int ci = (c0 - c_begin) >> 5;  // chunk index within this warp's columns
           const int k = md == 2 ? ci % kRedBuf : nred % kRedBuf;
           const bool keep = md == 2 && epi.keeps(mt, nt);
@@ -546,7 +578,8 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
                            cudaStream_t st) {
   const dim3 block(64 + 32 * EPIW);
   const int stage_extra_single = Epi::kStage ? red_stage_bytes<C, EPIW>() : 0;
-  if (m_tiles % 2 == 0 && C::kBTiles == 2) {
+  if constexpr (C::kBTiles == 2) {
+   if (m_tiles % 2 == 0) {
     // CTA pairs: clusters of two, as many as fit at once
     using CP = PairCfg<C, 6, 2>;
     constexpr int kStagePair = (CP::kSa + CP::kSb) * CP::kHalfBytes;
@@ -572,6 +605,7 @@ int launch_gemm_persistent(const TileMapParams& p, int n_tiles, int m_tiles, int
     NED_CUDA(cudaLaunchKernelEx(&cfg, kern, p, epi, n_tiles, m_tiles, batch));
     NED_LAUNCH_CHECK("umma_gemm_persistent_kernel");
     return NEDMFT_OK;
+   }
   }
   const int smem_bytes = C::kSmem + stage_extra_single;
   auto kern = umma_gemm_persistent_kernel<C, Pairs, Epi, EPIW, 1>;
@@ -693,19 +727,19 @@ struct EpiUpdate {
       }
     }
     if (in_block(mt * kTileRows, kn)) {
-      // row block Kn: row c = i - kn of A_{Kn,:}, embedded and transposed
-      // (A_{Kn,Kn} -> I): column j gives rows 2j, 2j+1 of the image at
-      // k = 2c, 2c+1.  A 16-byte core-matrix row holds k = 2c .. 2c+7 of one
-      // row, i.e. 4 consecutive c: each quad of lanes transposes its values
-      // (a 4 x 4 transpose of 16-byte elements in two xor exchanges) so that
-      // lane l of the quad writes whole rows of column j0 + 4 jq + l.
+      // row block Kn: row c = i - kn of A_{Kn,:} (A_{Kn,Kn} -> I) as (Re, Im)
+      // pairs over k: column j gives row j of the image at k = 2c, 2c+1.  A
+      // 16-byte core-matrix row holds k = 2c .. 2c+7 of one row, i.e. 4
+      // consecutive c: each quad of lanes transposes its values (a 4 x 4
+      // transpose of 16-byte elements in two xor exchanges) so that lane l of
+      // the quad writes whole rows of column j0 + 4 jq + l.
       __nv_bfloat16* td = timg + b * pstride;
       const int c = i - kn;
       const int l = r & 3;
       const int cq = c - l;
 #pragma unroll
       for (int jq = 0; jq < 4; ++jq) {
-        uint4 e[4];  // e[p]: (row 2j hi, row 2j+1 hi, row 2j lo, row 2j+1 lo) at k = 2c, j = j0 + 4 jq + p
+        uint4 e[4];  // e[p]: (hi, lo) at k = 2c of column j = j0 + 4 jq + p
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const int u = 4 * jq + p;
@@ -713,52 +747,50 @@ struct EpiUpdate {
           float re = (u & 1) ? o[u >> 1].z : o[u >> 1].x;
           float im = (u & 1) ? o[u >> 1].w : o[u >> 1].y;
           if (in_block(j, kn)) { re = (j - kn == c) ? 1.f : 0.f; im = 0.f; }
-          __nv_bfloat16 rh, rl, ih, il, nh, nl;
+          __nv_bfloat16 rh, rl, ih, il;
           split2(re, rh, rl);
           split2(im, ih, il);
-          split2(-im, nh, nl);
-          const __nv_bfloat162 a0 = __halves2bfloat162(rh, nh), a1 = __halves2bfloat162(ih, rh);
-          const __nv_bfloat162 a2 = __halves2bfloat162(rl, nl), a3 = __halves2bfloat162(il, rl);
-          e[p] = make_uint4(*reinterpret_cast<const uint32_t*>(&a0), *reinterpret_cast<const uint32_t*>(&a1),
-                            *reinterpret_cast<const uint32_t*>(&a2), *reinterpret_cast<const uint32_t*>(&a3));
+          e[p] = make_uint4(bf2_bits(rh, ih), bf2_bits(rl, il), 0u, 0u);
         }
         quad_transpose4(e, l);  // e[m]: lane m's element for p = l
         const int j = j0 + 4 * jq + l;
-        const size_t o0 = img_offset(2 * j, 2 * cq, kKtW), o1 = img_offset(2 * j + 1, 2 * cq, kKtW);
+        const size_t o0 = img_offset(j, 2 * cq, kKtW);
         *reinterpret_cast<uint4*>(td + o0) = make_uint4(e[0].x, e[1].x, e[2].x, e[3].x);
-        *reinterpret_cast<uint4*>(td + o1) = make_uint4(e[0].y, e[1].y, e[2].y, e[3].y);
-        *reinterpret_cast<uint4*>(td + tslice + o0) = make_uint4(e[0].z, e[1].z, e[2].z, e[3].z);
-        *reinterpret_cast<uint4*>(td + tslice + o1) = make_uint4(e[0].w, e[1].w, e[2].w, e[3].w);
+        *reinterpret_cast<uint4*>(td + tslice + o0) = make_uint4(e[0].y, e[1].y, e[2].y, e[3].y);
       }
     }
   }
 };
 
-// R (W x np complex, acc rows = R rows) -> the update's B operand image:
-// rows n = 2j, 2j+1; k = 2r, 2r+1 with [[re, -im], [im, re]].
+// R (W x np complex; accumulator 0 = Re R, 1 = Im R, rows = R rows, columns
+// = complex columns j) -> the update's B operand image: rows n = 2j, 2j+1;
+// k = 2r, 2r+1 with [[re, -im], [im, re]].
 template <int W>
 struct EpiRPack {
   static constexpr bool kStage = false;
   static constexpr int kKtW = 2 * W / kTileK;
+  static constexpr int kBn = 128;  // complex columns per tile
   __device__ int mode(int, int) const { return 1; }
   __nv_bfloat16* img;   // per matrix: 2 slices x (2 np x 2 W)
   size_t bstride;       // elements between matrices
   size_t slice;         // elements between slices
-  // row r of R, columns of the chunk: rows 2j, 2j+1 of the image at k = 2r,
-  // 2r+1; a quad of lanes (4 consecutive r) exchanges its values so that each
-  // lane writes whole 16-byte core-matrix rows (see EpiUpdate's Aᵀ panel)
-  __device__ void operator()(int b, int mt, int nt, int r_tile, int c0, const float* v) const {
+  // row r of R, complex columns j0 .. j0+31: rows 2j, 2j+1 of the image at
+  // k = 2r, 2r+1; a quad of lanes (4 consecutive r) exchanges its values so
+  // that each lane writes whole 16-byte core-matrix rows (see EpiUpdate's
+  // A_K panel)
+  __device__ void operator()(int b, int mt, int nt, int r_tile, int c0, const float* re_v,
+                             const float* im_v) const {
     __nv_bfloat16* base = img + b * bstride;
     const int r = mt * kTileRows + r_tile;  // row of R
     const int l = r_tile & 3, rq = r - l;
-    const int j0 = (nt * CfgGJ::kBn + c0) >> 1;
+    const int j0 = nt * kBn + c0;
 #pragma unroll
-    for (int jq = 0; jq < 4; ++jq) {
+    for (int jq = 0; jq < 8; ++jq) {
       uint4 e[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int u = 4 * jq + p;
-        const float re = v[2 * u], im = v[2 * u + 1];
+        const float re = re_v[u], im = im_v[u];
         __nv_bfloat16 rh, rl, ih, il, nh, nl;
         split2(re, rh, rl);
         split2(im, ih, il);
@@ -780,7 +812,8 @@ struct EpiRPack {
 
 
 // P = inv(A_KK) (kNb x kNb, FP32, no pivoting -- the static row order makes
-// the pivots safe) written as the R-product's A operand: row r, k = 2c / 2c+1.
+// the pivots safe) written as the R-product's A operand (P' and P'', row r,
+// k = 2c / 2c+1).
 // A_KK sits in shared memory and is inverted in two 64-column halves (block
 // Gauss-Jordan):
 //   B11 <- P1 = inv(A11);  B12 <- P1 A12;  B22 <- A22 - A21 B12;  B21 <- -A21 P1;
@@ -938,6 +971,28 @@ __device__ __forceinline__ void piv_neg(float2 (&v)[4][2]) {
     for (int c = 0; c < 2; ++c) v[a][c] = make_float2(-v[a][c].x, -v[a][c].y);
 }
 
+// Four entries z[0..3] of a row of P (consecutive columns) as the R
+// product's A operand: a 16-byte core-matrix row of each of the four slices,
+// P' = (Re P, -Im P) hi, lo and P'' = (Im P, Re P) hi, lo, `slice` apart.
+__device__ __forceinline__ void piv_store4(__nv_bfloat16* dst, size_t slice, size_t o, const float2 (&z)[4]) {
+  uint32_t h1[4], l1[4], h2[4], l2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat16 rh, rl, ih, il, nh, nl;
+    split2(z[q].x, rh, rl);
+    split2(z[q].y, ih, il);
+    split2(-z[q].y, nh, nl);
+    h1[q] = bf2_bits(rh, nh);
+    l1[q] = bf2_bits(rl, nl);
+    h2[q] = bf2_bits(ih, rh);
+    l2[q] = bf2_bits(il, rl);
+  }
+  *reinterpret_cast<uint4*>(dst + o) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+  *reinterpret_cast<uint4*>(dst + slice + o) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
+  *reinterpret_cast<uint4*>(dst + 2 * slice + o) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+  *reinterpret_cast<uint4*>(dst + 3 * slice + o) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
+}
+
 __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __restrict__ A, int np, int k0,
                                                              __nv_bfloat16* __restrict__ pimg, size_t pstride,
                                                              size_t pslice, int* status) {
@@ -1014,19 +1069,10 @@ __global__ void __launch_bounds__(1024) gj_pivot_pack_kernel(const float2* __res
     const int r = t >> 3, cg = 16 * (t & 7);
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      uint32_t hi[4], lo[4];
+      float2 z[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 z = M[r * kNb + cg + 4 * h + q];
-        __nv_bfloat16 rh, rl, ih, il;
-        split2(z.x, rh, rl);
-        split2(z.y, ih, il);
-        hi[q] = bf2_bits(rh, ih);
-        lo[q] = bf2_bits(rl, il);
-      }
-      const size_t o = img_offset(r, 2 * (cg + 4 * h), kKt);
-      *reinterpret_cast<uint4*>(dst + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(dst + pslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      for (int q = 0; q < 4; ++q) z[q] = M[r * kNb + cg + 4 * h + q];
+      piv_store4(dst, pslice, img_offset(r, 2 * (cg + 4 * h), kKt), z);
     }
   }
 }
@@ -1046,8 +1092,8 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const float2* __restric
   }
 }
 
-// P = inv(A_KK) (W x W, FP32) as the R-product's A operand: row r, k = 2c /
-// 2c+1.  Block (x, y): rows 8x .. 8x+7 of matrix y (one 8-row group); a
+// P = inv(A_KK) (W x W, FP32) as the R-product's A operand (P' and P'' hi,
+// lo: row r, k = 2c / 2c+1).  Block (x, y): rows 8x .. 8x+7 of matrix y (one 8-row group); a
 // thread takes 4 consecutive entries, one 16-byte core-matrix row per slice,
 // and 8 consecutive threads the 8 rows of one 128-byte core matrix.
 template <int W>
@@ -1062,23 +1108,13 @@ __global__ void __launch_bounds__(256) gj_ppack_kernel(const float2* __restrict_
     const float4 z01 = src[0], z23 = src[1];
     const float2 z[4] = {make_float2(z01.x, z01.y), make_float2(z01.z, z01.w), make_float2(z23.x, z23.y),
                          make_float2(z23.z, z23.w)};
-    uint32_t hi[4], lo[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __nv_bfloat16 rh, rl, ih, il;
-      split2(z[q].x, rh, rl);
-      split2(z[q].y, ih, il);
-      hi[q] = bf2_bits(rh, ih);
-      lo[q] = bf2_bits(rl, il);
-    }
-    const size_t o = img_offset(r, 2 * c4, 2 * W / kTileK);
-    *reinterpret_cast<uint4*>(dst + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(dst + pslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    piv_store4(dst, pslice, img_offset(r, 2 * c4, 2 * W / kTileK), z);
   }
 }
 
 // Block x of matrix y: rows x*128 .. +127 of C' (the update's A operand) and
-// columns x*128 .. +127 of the embedded A_{K,:}^T (the R-product's B operand),
+// columns x*128 .. +127 of A_{K,:}^T as (Re, Im) pairs over k (the R-product's
+// B operand),
 // for a block K of W columns.  A thread takes 4 consecutive columns c of C'
 // (one 16-byte core-matrix row per slice) or 4 consecutive rows c of A_{K,:}
 // at one column j (consecutive threads: consecutive j, coalesced loads).
@@ -1114,27 +1150,22 @@ __global__ void __launch_bounds__(256) gj_panel_pack_kernel(const float2* __rest
       *reinterpret_cast<uint4*>(cd + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(cd + cslice + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
-    {  // T rows 2j, 2j+1 at k = 2 c4 .. 2 c4 + 7 from A_{K,:}[c4 .. c4+3][j]
+    {  // T row j at k = 2 c4 .. 2 c4 + 7: (Re, Im) of A_{K,:}[c4 .. c4+3][j]
       const int j = base + (e & 127), c4 = 4 * (e >> 7);
       const bool in = (j >= k0 && j < k0 + W);
-      uint32_t h0[4], h1[4], l0[4], l1[4];
+      uint32_t h0[4], l0[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float2 z = in ? make_float2(j - k0 == c4 + q ? 1.f : 0.f, 0.f) : src[(size_t)(k0 + c4 + q) * np + j];
-        __nv_bfloat16 rh, rl, ih, il, nh, nl;
+        __nv_bfloat16 rh, rl, ih, il;
         split2(z.x, rh, rl);
         split2(z.y, ih, il);
-        split2(-z.y, nh, nl);
-        h0[q] = bf2_bits(rh, nh);
-        h1[q] = bf2_bits(ih, rh);
-        l0[q] = bf2_bits(rl, nl);
-        l1[q] = bf2_bits(il, rl);
+        h0[q] = bf2_bits(rh, ih);
+        l0[q] = bf2_bits(rl, il);
       }
-      const size_t o0 = img_offset(2 * j, 2 * c4, kKtW), o1 = img_offset(2 * j + 1, 2 * c4, kKtW);
+      const size_t o0 = img_offset(j, 2 * c4, kKtW);
       *reinterpret_cast<uint4*>(td + o0) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
-      *reinterpret_cast<uint4*>(td + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
       *reinterpret_cast<uint4*>(td + tslice + o0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
-      *reinterpret_cast<uint4*>(td + tslice + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
     }
   }
 }
@@ -1155,10 +1186,10 @@ template <int W>
 GjBuffers gj_buffers(int np) {
   GjBuffers g{};
   g.mat = align16k(sizeof(float2) * (size_t)np * np);
-  g.pimg = align16k(2 * sizeof(__nv_bfloat16) * (size_t)W * 2 * W);
-  g.cimg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);
-  g.timg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * W);
-  g.rimg = g.timg / 2;
+  g.pimg = align16k(4 * sizeof(__nv_bfloat16) * (size_t)W * 2 * W);           // P', P'' hi / lo
+  g.cimg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);      // C' hi / lo, two panels
+  g.timg = 2 * align16k(2 * sizeof(__nv_bfloat16) * (size_t)np * 2 * W);      // A_K^T hi / lo, two panels
+  g.rimg = align16k(2 * sizeof(__nv_bfloat16) * (size_t)2 * np * 2 * W);      // R embedded hi / lo
   if constexpr (W > 128) {
     const GjBuffers in = gj_buffers<128>(W);
     g.inner = in.mat + in.scratch;
@@ -1258,7 +1289,8 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
   __nv_bfloat16* rimg = reinterpret_cast<__nv_bfloat16*>(scratch + g.pimg + g.cimg + g.timg);
   const size_t pstride = per / 2, pslice = (size_t)W * 2 * W;
   const size_t cslice = (size_t)np * 2 * W;
-  const size_t tslice = (size_t)2 * np * 2 * W;
+  const size_t tslice = (size_t)np * 2 * W;
+  const size_t rslice = (size_t)2 * np * 2 * W;
   // the C' / A_K^T panels alternate between two buffers: step k reads buffer
   // k & 1 while its update writes step k+1's panels into the other one
   const size_t chalf = g.cimg / 2 / sizeof(__nv_bfloat16), thalf = g.timg / 2 / sizeof(__nv_bfloat16);
@@ -1302,16 +1334,16 @@ int gj_blocked_umma_w(float2* A, int n, int np, int nb, char* scratch, int* stat
       gj_ppack_kernel<W><<<dim3(W / kPackRows, nb), 256, 0, st>>>(Xs, pimg, pstride, pslice);
       NED_LAUNCH_CHECK("gj_ppack_kernel");
     }
-    {  // R = P A_{K,:}, W x 2np, K = 2W
+    {  // Re R = P' A_K, Im R = P'' A_K: W x np each, K = 2W
       TileMapParams p{tile_map, tile_of(pimg), per_t, (long long)(pslice / kTileElems),
                       tile_of(cur_t), per_t, (long long)(tslice / kTileElems), kKtW, status};
-      EpiRPack<W> epi{rimg, pstride, tslice};
-      int rc = launch_gemm_persistent<CfgGJH, Split3, 4>(p, 2 * np / CfgGJ::kBn, W / kTileRows, nb, epi, st);
+      EpiRPack<W> epi{rimg, pstride, rslice};
+      int rc = launch_gemm_persistent<CfgRP, Split3x2, 4>(p, np / EpiRPack<W>::kBn, W / kTileRows, nb, epi, st);
       if (rc) return rc;
     }
     {  // A <- A - C' R, np x 2np, K = 2W; next step's panels from the epilogue
       TileMapParams p{tile_map, tile_of(cur_c), per_t, (long long)(cslice / kTileElems),
-                      tile_of(rimg), per_t, (long long)(tslice / kTileElems), kKtW, status};
+                      tile_of(rimg), per_t, (long long)(rslice / kTileElems), kKtW, status};
       const int kn = (k0 + W < np) ? k0 + W : -1;
       EpiUpdate<W> epi{reinterpret_cast<float*>(A), (size_t)2 * np * np, np, k0, kn, nxt_c, nxt_t, pstride, cslice,
                        tslice};
