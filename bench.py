@@ -248,8 +248,10 @@ def load_peaks():
 # DRAM bytes of one Gauss-Jordan update launch (152 matrices at N_c = 1500) from
 # an ncu capture of the kernel as it stands; None while the kernel has changed
 # since the counters were taken
-UPDATE_TRAFFIC_BYTES = None
-UPDATE_TRAFFIC_NOTE = None
+UPDATE_TRAFFIC_BYTES = 6.33e9
+UPDATE_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 16 matrices "
+                       "(396.8 + 269.1 MB), scaled by 152/16 to the 152-matrix launch; 1.10x the "
+                       "algorithmic 2 x N_c^2 x 8 B per matrix: the rest is the C' and R operand panels")
 
 
 def roofline_for(precision: str, tflops: float, gbs: float, peaks, src: str):
