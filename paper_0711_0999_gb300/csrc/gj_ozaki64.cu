@@ -1,0 +1,243 @@
+// FP64-accurate trailing update of the pivoted Gauss-Jordan inversion (the
+// impurity step) on the tensor cores:  A <- A (rows and columns of the block K
+// zeroed) - C R  with C = A_{:,K} (np x 32 complex) and R = P A_{K,:} (32 x np).
+//
+// Ozaki split: every row of C (64 reals, re and im interleaved over k) and
+// every row of the 2 x 2 real embedding of R (output column n, 64 reals) is
+// scaled by a power of two to below one and cut into kOz64S integer slices
+// of 7 bits, q_s = digits s of x 2^-e, so x = 2^e sum_s q_s 2^-7(s+1) up to
+// 2^-7 kOz64S.  A slice product sum_k q_a q_b is an integer below 2^20 and
+// the up-to-7 products of one order o = a + b below 2^23, so bf16 operands
+// with FP32 accumulation in TMEM give every order's sum exactly.  The 28
+// products of order <= 6 leave a truncation near 1e-15 of the row and column
+// maxima (FP64 level); the epilogue adds the order sums, scaled by
+// 2^-7(o+2), in double-float (FP32 pairs, 48 bits) and subtracts the result
+// from A in FP64.
+#include "lattice.cuh"
+#include "umma_core.cuh"
+
+namespace nedmft {
+
+using namespace umma;
+
+namespace {
+
+constexpr int kOz64S = 7;     // slices per operand
+constexpr int kOz64Bits = 7;  // bits per slice
+constexpr int kOz64K = 64;    // K of the rank-32 complex update (re, im interleaved)
+constexpr int kOz64Bn = 64;   // output real columns per tile
+constexpr int kOz64Orders = kOz64S;  // orders 0 .. kOz64S - 1 are kept
+
+__device__ __forceinline__ void two_sum64(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Slices of the rows of C (np rows) and of the embedded R (2 np rows), one warp
+// per row: lane l takes k = 2l, 2l+1.  Row images in the canonical K-major
+// layout (one 128-row tile of 64 k per 128 rows), slice s at s * slice.
+__global__ void __launch_bounds__(256) oz64_pack_kernel(const double2* __restrict__ Rbuf,
+                                                        const double2* __restrict__ Cbuf, int np,
+                                                        __nv_bfloat16* __restrict__ cimg, int* __restrict__ cexp,
+                                                        __nv_bfloat16* __restrict__ rimg, int* __restrict__ rexp) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= 3 * np) return;  // whole warps
+  double v0, v1;  // the lane's two entries, k = 2 lane, 2 lane + 1
+  __nv_bfloat16* img;
+  int* ex;
+  int row;
+  size_t slice;
+  if (warp < np) {  // row i of C: (Re, Im) of C[i][lane]
+    row = warp;
+    const double2 z = Cbuf[(size_t)row * 32 + lane];
+    v0 = z.x;
+    v1 = z.y;
+    img = cimg;
+    ex = cexp;
+    slice = (size_t)np * kOz64K;
+  } else {  // row n of the embedding of R: column j = n / 2, c = lane
+    row = warp - np;
+    const int j = row >> 1;
+    const double2 z = Rbuf[(size_t)lane * np + j];
+    if ((row & 1) == 0) { v0 = z.x; v1 = -z.y; }  // [re, -im]
+    else { v0 = z.y; v1 = z.x; }                  // [im, re]
+    img = rimg;
+    ex = rexp;
+    slice = (size_t)2 * np * kOz64K;
+  }
+  double m = fmax(fabs(v0), fabs(v1));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);  // m < 2^e
+  if (lane == 0) ex[row] = e;
+  double r0 = ldexp(v0, -e), r1 = ldexp(v1, -e);
+  const size_t o = img_offset(row, 2 * lane, 1);
+#pragma unroll
+  for (int s = 0; s < kOz64S; ++s) {
+    const double q0 = rint(ldexp(r0, kOz64Bits)), q1 = rint(ldexp(r1, kOz64Bits));
+    r0 = ldexp(r0, kOz64Bits) - q0;
+    r1 = ldexp(r1, kOz64Bits) - q1;
+    *reinterpret_cast<__nv_bfloat162*>(img + s * slice + o) =
+        __halves2bfloat162(__float2bfloat16_rn((float)q0), __float2bfloat16_rn((float)q1));
+  }
+}
+
+struct Oz64Smem {
+  static constexpr int kA = kOz64S * kTileBytes;      // 128 rows x 64 k per slice
+  static constexpr int kB = kOz64S * kTileBytes / 2;  // 64 rows x 64 k per slice
+  static constexpr int kBytes = kA + kB + 1024 /*align*/ + 64 /*barriers*/;
+};
+
+// One CTA per output tile (128 rows, 64 real columns = 32 complex) of the
+// np x 2np real image of A.  Thread 0 brings the tile's 7 + 7 slice blocks in
+// with bulk copies, then issues the 28 products of order <= 6 (4 MMAs of
+// K = 16 each) into 7 order accumulators of 64 TMEM columns; 4 warps drain
+// them (one TMEM lane per row).  Column j of A is written iff (wlo <= j <
+// whi) == inside (the look-ahead window: see pivot_inverse).
+__global__ void __launch_bounds__(128, 1) oz64_update_kernel(double2* __restrict__ A, int np, int k0,
+                                                             const __nv_bfloat16* __restrict__ cimg,
+                                                             const int* __restrict__ cexp,
+                                                             const __nv_bfloat16* __restrict__ rimg,
+                                                             const int* __restrict__ rexp, int wlo, int whi,
+                                                             bool inside, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sa = smem;
+  unsigned char* sb = smem + Oz64Smem::kA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Oz64Smem::kA + Oz64Smem::kB);  // [0] loads, [1] products
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int mt = blockIdx.y, nt = blockIdx.x;  // 128-row tile, 64-column tile of the real image
+  const int n0 = nt * kOz64Bn;                 // first real column (2 j0)
+  // a tile wholly inside the skipped window: nothing to do
+  const int j_lo = n0 / 2, j_hi = j_lo + kOz64Bn / 2;
+  if (!inside && j_lo >= wlo && j_hi <= whi) return;
+  if (inside && (j_hi <= wlo || j_lo >= whi)) return;
+  constexpr uint32_t kCols = 512;  // 7 x 64 columns, allocated as a power of two
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const size_t cslice = (size_t)np * kOz64K, rslice = (size_t)2 * np * kOz64K;
+  if (t == 0) {
+    mbar_arrive_expect_tx(&bars[0], Oz64Smem::kA + Oz64Smem::kB);
+    for (int s = 0; s < kOz64S; ++s) {
+      // the canonical image: 128-row tile mt of slice s (16 KB); 64 rows of
+      // tile n0 / 128 starting at row n0 % 128 (8 KB, 8-row groups contiguous)
+      bulk_g2s(sa + s * kTileBytes, cimg + s * cslice + (size_t)mt * kTileElems, kTileBytes, &bars[0]);
+      bulk_g2s(sb + s * (kTileBytes / 2),
+               rimg + s * rslice + (size_t)(n0 >> 7) * kTileElems + (size_t)(n0 & 127) * 64, kTileBytes / 2,
+               &bars[0]);
+    }
+  }
+  bool ok = __syncthreads_and(mbar_wait(&bars[0], 0, abort_flag));
+  if (ok && t == 0) {
+    tc_fence_after();
+    constexpr uint32_t idesc = idesc_bf16(128, kOz64Bn);
+    for (int a = 0; a < kOz64S; ++a)
+      for (int b = 0; a + b < kOz64Orders; ++b)
+#pragma unroll
+        for (int kk = 0; kk < kOz64K / 16; ++kk)
+          mma_bf16(tmem + (uint32_t)(a + b) * kOz64Bn, smem_desc(smem_u32(sa + a * kTileBytes) + kk * 256, 128, 1024),
+                   smem_desc(smem_u32(sb + b * (kTileBytes / 2)) + kk * 256, 128, 1024), idesc,
+                   (a > 0 || kk > 0) ? 1u : 0u);
+  }
+  if (t == 0) mma_commit(&bars[1]);  // after every product issued above (also after a failed load wait)
+  {
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(&bars[1], 0) && global_ns() - t0 < kDrainNs) {
+    }
+    // no copy may be left in flight at exit (only after a failed wait)
+    if (!ok && t == 0)
+      while (!mbar_test(&bars[0], 0) && global_ns() - t0 < kDrainNs) {
+      }
+  }
+  tc_fence_after();
+  if (ok) {
+    const int i = mt * 128 + warp * 32 + lane;  // this thread's row
+    const bool ik = i >= k0 && i < k0 + 32;
+    const int ei = cexp[i];
+    for (int c0 = 0; c0 < kOz64Bn; c0 += 32) {
+      float hi[32], lo[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, hi);
+#pragma unroll
+      for (int u = 0; u < 32; ++u) lo[u] = 0.f;
+      for (int o = 1; o < kOz64Orders; ++o) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)o * kOz64Bn + c0, v);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          float s, e;
+          two_sum64(hi[u], ldexpf(v[u], -kOz64Bits * o), s, e);
+          hi[u] = s;
+          lo[u] += e;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 32; u += 2) {
+        const int n = n0 + c0 + u, j = n >> 1;
+        if ((j >= wlo && j < whi) != inside) continue;
+        const bool jk = j >= k0 && j < k0 + 32;
+        // order sums carry 2^-7(o+2) 2^(ei + en): o is in the ldexpf above
+        const int s0 = ei + rexp[n] - 2 * kOz64Bits, s1 = ei + rexp[n + 1] - 2 * kOz64Bits;
+        const double re = ldexp((double)hi[u] + (double)lo[u], s0);
+        const double im = ldexp((double)hi[u + 1] + (double)lo[u + 1], s1);
+        double2* a = A + (size_t)i * np + j;
+        const double2 old = (ik || jk) ? make_double2(0.0, 0.0) : *a;
+        *a = make_double2(old.x - re, old.y - im);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kCols);
+  }
+  if (t == 0 && *abort_flag && status) atomicCAS(status, 0, DS_TIMEOUT);
+}
+
+}  // namespace
+
+size_t oz64_workspace(int np) {
+  return align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * np * kOz64K) +
+         align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * 2 * np * kOz64K) + align256(sizeof(int) * (size_t)np) +
+         align256(sizeof(int) * (size_t)2 * np);
+}
+
+int oz64_prepare() {
+  return ensure_dyn_smem(reinterpret_cast<const void*>(oz64_update_kernel), Oz64Smem::kBytes);
+}
+
+int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* Cbuf, int wlo, int whi, bool inside,
+                void* ws, cudaStream_t st, int* status) {
+  if (np % 128) return set_error(NEDMFT_EINVAL, "oz64_update: np = %d not a multiple of 128", np);
+  char* p = static_cast<char*>(ws);
+  __nv_bfloat16* cimg = reinterpret_cast<__nv_bfloat16*>(p);
+  p += align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * np * kOz64K);
+  __nv_bfloat16* rimg = reinterpret_cast<__nv_bfloat16*>(p);
+  p += align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * 2 * np * kOz64K);
+  int* cexp = reinterpret_cast<int*>(p);
+  p += align256(sizeof(int) * (size_t)np);
+  int* rexp = reinterpret_cast<int*>(p);
+  const int warps = 3 * np;
+  oz64_pack_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(Rbuf, Cbuf, np, cimg, cexp, rimg, rexp);
+  NED_LAUNCH_CHECK("oz64_pack_kernel");
+  if (int rc = oz64_prepare()) return rc;
+  oz64_update_kernel<<<dim3(2 * np / kOz64Bn, np / 128), 128, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg,
+                                                                                      rexp, wlo, whi, inside, status);
+  NED_LAUNCH_CHECK("oz64_update_kernel");
+  return NEDMFT_OK;
+}
+
+}  // namespace nedmft

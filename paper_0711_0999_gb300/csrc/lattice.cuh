@@ -32,5 +32,11 @@ int launch_finish_current(int nt, const double2* jacc, double* j, double* ji, cu
 size_t pivot_inverse_workspace(int n);
 int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status);
 int pivot_inverse_prepare();  // before capturing pivot_inverse into a graph
+// FP64-accurate trailing update of pivot_inverse on the tensor cores (Ozaki
+// split); np a multiple of 128; columns j written iff (wlo <= j < whi) == inside.
+size_t oz64_workspace(int np);
+int oz64_prepare();  // sets the update kernel's shared-memory limit
+int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* Cbuf, int wlo, int whi, bool inside,
+                void* ws, cudaStream_t st, int* status);
 
 }  // namespace nedmft

@@ -644,11 +644,11 @@ __global__ void unpermute_kernel(const double2* __restrict__ x, int np, int n, c
 }
 
 size_t pivot_inverse_workspace(int n) {
-  const int np = ((n + 63) / 64) * 64;
+  const int np = ((n + 127) / 128) * 128;
   const int nchunk = (n + kTourRows - 1) / kTourRows;
   return align256(sizeof(double2) * (size_t)np * np) + align256(sizeof(double2) * kTourNB * kTourNB) +
          2 * align256(sizeof(double2) * (size_t)kTourNB * np) + 2 * align256(sizeof(int) * (size_t)nchunk * kTourNB) +
-         2 * align256(sizeof(int) * (size_t)n) + align256(sizeof(int) * (1 + 4 * kTourNB));
+         2 * align256(sizeof(int) * (size_t)n) + align256(sizeof(int) * (1 + 4 * kTourNB)) + oz64_workspace(np);
 }
 
 // Second stream (highest priority) and two events per device and host
@@ -682,7 +682,7 @@ int look_ahead(LookAhead** out) {
 int pivot_inverse_prepare() {
   LookAhead* la = nullptr;
   int rc = look_ahead(&la);
-  if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<kTourNB>), (int)upd_smem_bytes<kTourNB>());
+  if (!rc) rc = oz64_prepare();
   if (!rc)
     rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)(sizeof(float2) * kTourRows * (kTourNB + 1)));
   return rc;
@@ -696,7 +696,7 @@ int pivot_inverse_prepare() {
 // k + 1 wait for both.
 int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   constexpr int NB = kTourNB;
-  const int np = ((n + 63) / 64) * 64;
+  const int np = ((n + 127) / 128) * 128;  // 128-row tiles of the tensor-core update
   const int nchunk = (n + kTourRows - 1) / kTourRows;
   char* p = static_cast<char*>(ws);
   double2* ap = reinterpret_cast<double2*>(p); p += align256(sizeof(double2) * (size_t)np * np);
@@ -708,7 +708,8 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   cand[1] = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)nchunk * NB);
   int* piv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
   int* inv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
-  int* gather = reinterpret_cast<int*>(p);
+  int* gather = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (1 + 4 * kTourNB));
+  void* ozws = p;
   LookAhead* la = nullptr;
   int rc = look_ahead(&la);
   if (rc) return rc;
@@ -717,11 +718,8 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   if (bx > 152 * 8) bx = 152 * 8;
   pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np);
   NED_LAUNCH_CHECK("pad_identity_kernel");
-  const size_t upd_smem = upd_smem_bytes<NB>();
   const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
-  rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<NB>), (int)upd_smem);
-  if (!rc) rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem);
-  if (rc) return rc;
+  if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem))) return rc;
   // tournament over the rows k0 .. n-1 on the panel columns k0 .. k0+31, then
   // the inverse of the winners' 32 x 32 block (read in their rows, before the
   // swaps), on stream s
@@ -751,9 +749,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     NED_LAUNCH_CHECK("gj_panels_kernel");
     const int k1 = k0 + NB;  // the next step
     if (k1 >= n) {
-      gj_update_kernel<NB><<<dim3(np / 64, np / 64, 1), kUpdThreads, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, 0, 0,
-                                                                                    false);
-      NED_LAUNCH_CHECK("gj_update_kernel");
+      if ((rc = oz64_update(ap, np, k0, rbuf, cbuf, 0, 0, false, ozws, st, status))) return rc;
       break;
     }
     // side stream: this step's update of the next panel's columns, then the
@@ -764,9 +760,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     NED_LAUNCH_CHECK("gj_update_window_kernel");
     if ((rc = chain(k1, la->side))) return rc;
     NED_CUDA(cudaEventRecord(la->chain, la->side));
-    gj_update_kernel<NB><<<dim3(np / 64, np / 64, 1), kUpdThreads, upd_smem, st>>>(ap, np, k0, rbuf, cbuf, 0, k1,
-                                                                                  k1 + NB, false);
-    NED_LAUNCH_CHECK("gj_update_kernel");
+    if ((rc = oz64_update(ap, np, k0, rbuf, cbuf, k1, k1 + NB, false, ozws, st, status))) return rc;
     NED_CUDA(cudaStreamWaitEvent(st, la->chain, 0));
   }
   swap_colmap_kernel<<<1, 1, 0, st>>>(n, piv, inv);
