@@ -5,8 +5,8 @@
 // Ozaki split: every row of C (64 reals, re and im interleaved over k) and
 // every row of the 2 x 2 real embedding of R (output column n, 64 reals) is
 // scaled by a power of two to below one and cut into kOz64S integer slices
-// of 7 bits, q_s = digits s of x 2^-e, so x = 2^e sum_s q_s 2^-7(s+1) up to
-// 2^-7 kOz64S.  A slice product sum_k q_a q_b is an integer below 2^20 and
+// of 7 bits (balanced base-128 digits of x 2^-e), so x = 2^e sum_s q_s
+// 2^-7(s+1) up to 2^-7 kOz64S.  A slice product sum_k q_a q_b is below 2^21 and
 // the up-to-7 products of one order o = a + b below 2^23, so bf16 operands
 // with FP32 accumulation in TMEM give every order's sum exactly.  The 28
 // products of order <= 6 leave a truncation near 1e-15 of the row and column
@@ -34,53 +34,67 @@ __device__ __forceinline__ void two_sum64(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Slices of the rows of C (np rows) and of the embedded R (2 np rows), one warp
-// per row: lane l takes k = 2l, 2l+1.  Row images in the canonical K-major
-// layout (one 128-row tile of 64 k per 128 rows), slice s at s * slice.
-__global__ void __launch_bounds__(256) oz64_pack_kernel(const double2* __restrict__ Rbuf,
-                                                        const double2* __restrict__ Cbuf, int np,
-                                                        __nv_bfloat16* __restrict__ cimg, int* __restrict__ cexp,
-                                                        __nv_bfloat16* __restrict__ rimg, int* __restrict__ rexp) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= 3 * np) return;  // whole warps
-  double v0, v1;  // the lane's two entries, k = 2 lane, 2 lane + 1
-  __nv_bfloat16* img;
-  int* ex;
-  int row;
-  size_t slice;
-  if (warp < np) {  // row i of C: (Re, Im) of C[i][lane]
-    row = warp;
-    const double2 z = Cbuf[(size_t)row * 32 + lane];
-    v0 = z.x;
-    v1 = z.y;
-    img = cimg;
-    ex = cexp;
-    slice = (size_t)np * kOz64K;
-  } else {  // row n of the embedding of R: column j = n / 2, c = lane
-    row = warp - np;
-    const int j = row >> 1;
-    const double2 z = Rbuf[(size_t)lane * np + j];
-    if ((row & 1) == 0) { v0 = z.x; v1 = -z.y; }  // [re, -im]
-    else { v0 = z.y; v1 = z.x; }                  // [im, re]
-    img = rimg;
-    ex = rexp;
-    slice = (size_t)2 * np * kOz64K;
-  }
+// The slices of one row (64 reals, lane l holding k = 2l, 2l+1): the row
+// exponent e (max |x| < 2^e) from a warp maximum, then X = round(x 2^(49-e)),
+// |X| < 2^49, cut into balanced base-128 digits from the bottom (six digits
+// in [-64, 63], the top one the rest, |q_0| <= 129; all exact in bf16), so
+// x = 2^e sum_s q_s 2^-7(s+1) up to 2^(e-50).  Integer work except two FP64
+// operations per value.
+__device__ __forceinline__ void oz64_slice_row(double v0, double v1, int row, int lane, __nv_bfloat16* img,
+                                               size_t slice, int* ex) {
   double m = fmax(fabs(v0), fabs(v1));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   int e = 0;
   if (m > 0.0) frexp(m, &e);  // m < 2^e
   if (lane == 0) ex[row] = e;
-  double r0 = ldexp(v0, -e), r1 = ldexp(v1, -e);
+  constexpr int kTop = kOz64Bits * kOz64S;  // 49
+  long long x0 = llrint(ldexp(v0, kTop - e)), x1 = llrint(ldexp(v1, kTop - e));
+  int q0[kOz64S], q1[kOz64S];
+#pragma unroll
+  for (int s = kOz64S - 1; s > 0; --s) {
+    const int d0 = (int)((x0 + 64) & 127) - 64, d1 = (int)((x1 + 64) & 127) - 64;
+    q0[s] = d0;
+    q1[s] = d1;
+    x0 = (x0 - d0) >> kOz64Bits;
+    x1 = (x1 - d1) >> kOz64Bits;
+  }
+  q0[0] = (int)x0;
+  q1[0] = (int)x1;
   const size_t o = img_offset(row, 2 * lane, 1);
 #pragma unroll
-  for (int s = 0; s < kOz64S; ++s) {
-    const double q0 = rint(ldexp(r0, kOz64Bits)), q1 = rint(ldexp(r1, kOz64Bits));
-    r0 = ldexp(r0, kOz64Bits) - q0;
-    r1 = ldexp(r1, kOz64Bits) - q1;
+  for (int s = 0; s < kOz64S; ++s)
     *reinterpret_cast<__nv_bfloat162*>(img + s * slice + o) =
-        __halves2bfloat162(__float2bfloat16_rn((float)q0), __float2bfloat16_rn((float)q1));
+        __halves2bfloat162(__float2bfloat16_rn((float)q0[s]), __float2bfloat16_rn((float)q1[s]));
+}
+
+// Slices of the rows of C (np rows, blocks 0 .. np/8 - 1: a warp per row) and
+// of the embedded R (2 np rows, blocks np/8 .. : 32 columns j of R per block,
+// read by rows of R into shared memory, then a warp per pair of rows 2j, 2j+1).
+// Row images in the canonical K-major layout (one 128-row tile of 64 k per
+// 128 rows), slice s at s * slice.
+__global__ void __launch_bounds__(256) oz64_pack_kernel(const double2* __restrict__ Rbuf,
+                                                        const double2* __restrict__ Cbuf, int np,
+                                                        __nv_bfloat16* __restrict__ cimg, int* __restrict__ cexp,
+                                                        __nv_bfloat16* __restrict__ rimg, int* __restrict__ rexp) {
+  __shared__ double2 tile[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cblocks = np / 8;
+  if ((int)blockIdx.x < cblocks) {  // row i of C: (Re, Im) of C[i][lane]
+    const int i = blockIdx.x * 8 + warp;
+    const double2 z = Cbuf[(size_t)i * 32 + lane];
+    oz64_slice_row(z.x, z.y, i, lane, cimg, (size_t)np * kOz64K, cexp);
+    return;
+  }
+  const int j0 = (blockIdx.x - cblocks) * 32;
+  for (int c = warp; c < 32; c += 8) tile[c][lane] = Rbuf[(size_t)c * np + j0 + lane];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = 4 * warp + q, j = j0 + jj;
+    const double2 z = tile[lane][jj];  // R[c = lane][j]
+    oz64_slice_row(z.x, -z.y, 2 * j, lane, rimg, (size_t)2 * np * kOz64K, rexp);     // [re, -im]
+    oz64_slice_row(z.y, z.x, 2 * j + 1, lane, rimg, (size_t)2 * np * kOz64K, rexp);  // [im, re]
   }
 }
 
@@ -230,8 +244,7 @@ int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* 
   int* cexp = reinterpret_cast<int*>(p);
   p += align256(sizeof(int) * (size_t)np);
   int* rexp = reinterpret_cast<int*>(p);
-  const int warps = 3 * np;
-  oz64_pack_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(Rbuf, Cbuf, np, cimg, cexp, rimg, rexp);
+  oz64_pack_kernel<<<np / 8 + np / 32, 256, 0, st>>>(Rbuf, Cbuf, np, cimg, cexp, rimg, rexp);
   NED_LAUNCH_CHECK("oz64_pack_kernel");
   if (int rc = oz64_prepare()) return rc;
   oz64_update_kernel<<<dim3(2 * np / kOz64Bn, np / 128), 128, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg,

@@ -546,51 +546,46 @@ __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restri
     __syncthreads();
   }
   if (t < kTourNB) out[c * kTourNB + t] = (t < steps) ? gidx[t] : -1;
-  if (final_round && t == 0) {
+  if (final_round) {
     // winners -> swap sequence: position k0 + j takes the row now at the
-    // winner's position; `pos`/`row_at` track the (<= 64) touched positions
-    int pos_key[2 * kTourNB], pos_row[2 * kTourNB], used = 0;
-    auto row_at = [&](int q) {
-      for (int u = 0; u < used; ++u)
-        if (pos_key[u] == q) return pos_row[u];
-      return q;
-    };
-    auto set_at = [&](int q, int r) {
-      for (int u = 0; u < used; ++u)
-        if (pos_key[u] == q) { pos_row[u] = r; return; }
-      pos_key[used] = q;
-      pos_row[used] = r;
-      ++used;
-    };
-    for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
-      const int w = j < steps ? gidx[j] : -1;
-      int target = k0 + j;
-      if (w >= 0) {
-        // current position of row w: a touched position holding it, else w itself
-        int where = -1;
-        for (int u = 0; u < used; ++u)
-          if (pos_row[u] == w) { where = pos_key[u]; break; }
-        if (where < 0) where = (row_at(w) == w) ? w : -1;
-        if (where >= 0) target = where;
-      } else if (status) {
-        atomicCAS(status, 0, DS_SINGULAR);  // fewer nonzero candidates than columns
-      }
-      piv[k0 + j] = target;
-      if (target != k0 + j) {
-        const int ra = row_at(k0 + j), rb = row_at(target);
-        set_at(k0 + j, rb);
-        set_at(target, ra);
-      }
-    }
-    if (gather) {
-      int cnt = 0;
-      for (int u = 0; u < used; ++u)
-        if (pos_row[u] != pos_key[u]) {
-          gather[1 + 2 * cnt] = pos_key[u];
-          gather[2 + 2 * cnt] = pos_row[u];
-          ++cnt;
+    // winner's position.  The positions and rows involved (<= 64) get slots:
+    // slot j < 32 for position k0 + j, slot 32 + j for winner j when it lies
+    // outside the block; row_at[slot] / where[slot] track which row sits at a
+    // position and where a row sits, so every swap is O(1)
+    __shared__ int row_at[2 * kTourNB], where_at[2 * kTourNB];
+    if (t < 2 * kTourNB) row_at[t] = where_at[t] = t;
+    __syncthreads();
+    if (t == 0) {
+      auto value = [&](int sl) { return sl < kTourNB ? k0 + sl : gidx[sl - kTourNB]; };
+      for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
+        const int w = j < steps ? gidx[j] : -1;
+        int target = k0 + j, tsl = j;
+        if (w >= 0) {
+          const int wsl = (w >= k0 && w < k0 + kTourNB) ? w - k0 : kTourNB + j;
+          tsl = where_at[wsl];
+          target = value(tsl);
+        } else if (status) {
+          atomicCAS(status, 0, DS_SINGULAR);  // fewer nonzero candidates than columns
         }
-      gather[0] = cnt;
+        piv[k0 + j] = target;
+        if (tsl != j) {
+          const int ra = row_at[j], rb = row_at[tsl];
+          row_at[j] = rb;
+          row_at[tsl] = ra;
+          where_at[ra] = tsl;
+          where_at[rb] = j;
+        }
+      }
+      if (gather) {
+        int cnt = 0;
+        for (int sl = 0; sl < 2 * kTourNB; ++sl)
+          if (row_at[sl] != sl) {
+            gather[1 + 2 * cnt] = value(sl);
+            gather[2 + 2 * cnt] = value(row_at[sl]);
+            ++cnt;
+          }
+        gather[0] = cnt;
+      }
     }
   }
 }
