@@ -107,10 +107,10 @@ struct Oz64Smem {
 // One CTA per output tile (128 rows, 64 real columns = 32 complex) of the
 // np x 2np real image of A.  Thread 0 brings the tile's 7 + 7 slice blocks in
 // with bulk copies, then issues the 28 products of order <= 6 (4 MMAs of
-// K = 16 each) into 7 order accumulators of 64 TMEM columns; 4 warps drain
-// them (one TMEM lane per row).  Column j of A is written iff (wlo <= j <
+// K = 16 each) into 7 order accumulators of 64 TMEM columns; 8 warps drain
+// them (one TMEM lane per row, two warps per lane quarter, 32 columns each).  Column j of A is written iff (wlo <= j <
 // whi) == inside (the look-ahead window: see pivot_inverse).
-__global__ void __launch_bounds__(128, 1) oz64_update_kernel(double2* __restrict__ A, int np, int k0,
+__global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict__ A, int np, int k0,
                                                              const __nv_bfloat16* __restrict__ cimg,
                                                              const int* __restrict__ cexp,
                                                              const __nv_bfloat16* __restrict__ rimg,
@@ -178,17 +178,18 @@ __global__ void __launch_bounds__(128, 1) oz64_update_kernel(double2* __restrict
   }
   tc_fence_after();
   if (ok) {
-    const int i = mt * 128 + warp * 32 + lane;  // this thread's row
+    const int i = mt * 128 + (warp & 3) * 32 + lane;  // this thread's row (TMEM lane)
     const bool ik = i >= k0 && i < k0 + 32;
     const int ei = cexp[i];
-    for (int c0 = 0; c0 < kOz64Bn; c0 += 32) {
+    {
+      const int c0 = 32 * (warp >> 2);  // warps 0-3 and 4-7 drain the two 32-column halves
       float hi[32], lo[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, hi);
+      tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0, hi);
 #pragma unroll
       for (int u = 0; u < 32; ++u) lo[u] = 0.f;
       for (int o = 1; o < kOz64Orders; ++o) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)o * kOz64Bn + c0, v);
+        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)o * kOz64Bn + c0, v);
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           float s, e;
@@ -202,13 +203,24 @@ __global__ void __launch_bounds__(128, 1) oz64_update_kernel(double2* __restrict
         const int n = n0 + c0 + u, j = n >> 1;
         if ((j >= wlo && j < whi) != inside) continue;
         const bool jk = j >= k0 && j < k0 + 32;
-        // order sums carry 2^-7(o+2) 2^(ei + en): o is in the ldexpf above
+        // order sums carry 2^-7(o+2) 2^(ei + en): o is in the ldexpf above.
+        // The power of two is applied in FP32 (exact) while the result stays
+        // well inside the FP32 range, else in FP64; then two conversions and
+        // two FP64 subtractions per value
         const int s0 = ei + rexp[n] - 2 * kOz64Bits, s1 = ei + rexp[n + 1] - 2 * kOz64Bits;
-        const double re = ldexp((double)hi[u] + (double)lo[u], s0);
-        const double im = ldexp((double)hi[u + 1] + (double)lo[u + 1], s1);
         double2* a = A + (size_t)i * np + j;
-        const double2 old = (ik || jk) ? make_double2(0.0, 0.0) : *a;
-        *a = make_double2(old.x - re, old.y - im);
+        double2 nv = (ik || jk) ? make_double2(0.0, 0.0) : *a;
+        if (s0 > -64 && s0 < 64) {
+          nv.x = (nv.x - (double)ldexpf(hi[u], s0)) - (double)ldexpf(lo[u], s0);
+        } else {
+          nv.x -= ldexp((double)hi[u] + (double)lo[u], s0);
+        }
+        if (s1 > -64 && s1 < 64) {
+          nv.y = (nv.y - (double)ldexpf(hi[u + 1], s1)) - (double)ldexpf(lo[u + 1], s1);
+        } else {
+          nv.y -= ldexp((double)hi[u + 1] + (double)lo[u + 1], s1);
+        }
+        *a = nv;
       }
     }
   }
@@ -247,7 +259,7 @@ int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* 
   oz64_pack_kernel<<<np / 8 + np / 32, 256, 0, st>>>(Rbuf, Cbuf, np, cimg, cexp, rimg, rexp);
   NED_LAUNCH_CHECK("oz64_pack_kernel");
   if (int rc = oz64_prepare()) return rc;
-  oz64_update_kernel<<<dim3(2 * np / kOz64Bn, np / 128), 128, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg,
+  oz64_update_kernel<<<dim3(2 * np / kOz64Bn, np / 128), 256, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg,
                                                                                       rexp, wlo, whi, inside, status);
   NED_LAUNCH_CHECK("oz64_update_kernel");
   return NEDMFT_OK;

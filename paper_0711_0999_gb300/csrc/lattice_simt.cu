@@ -223,18 +223,28 @@ __global__ void __launch_bounds__(256) gj_pivot32_fp64_kernel(const double2* __r
   };
   publish(0, 0);
   __syncthreads();
+  const int lane = t & 31;
   for (int k = 0; k < 32; ++k) {
     const int buf = k & 1;
     const double2 pinv = pinvb[buf];
+    // g = a_rk / a_kk once per row (the first of the row's 8 threads), shared
+    // by a shuffle: the FP64 units are the limit here
+    double2 g = make_double2(0.0, 0.0);
+    if ((t & 7) == 0) g = cmul(colb[buf][r], pinv);
+    g.x = __shfl_sync(0xffffffffu, g.x, lane & ~7);
+    g.y = __shfl_sync(0xffffffffu, g.y, lane & ~7);
     if (r == k) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = (c0 + u == k) ? pinv : cmul(v[u], pinv);
     } else {
-      const double2 g = cmul(colb[buf][r], pinv);  // a_rk / a_kk
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int j = c0 + u;
-        v[u] = (j == k) ? make_double2(-g.x, -g.y) : csub(v[u], cmul(g, rowb[buf][j]));
+        const double2 rb = rowb[buf][j];
+        // v - g rb in four FMAs
+        const double2 nv = make_double2(fma(-g.x, rb.x, fma(g.y, rb.y, v[u].x)),
+                                        fma(-g.x, rb.y, fma(-g.y, rb.x, v[u].y)));
+        v[u] = (j == k) ? make_double2(-g.x, -g.y) : nv;
       }
     }
     if (k + 1 < 32) publish(k + 1, buf ^ 1);
