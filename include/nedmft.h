@@ -356,7 +356,9 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  * D inv(A_h) D, and D (one entry per row, -U W_j at (j, j-1), +U W_0 at
  * (0, N-1)) makes the last product a gather.  Inversions: blocked
  * Gauss-Jordan (32 columns per step) whose pivot rows a tournament of
- * partial-pivoting rounds on 256-row chunks chooses; each step's tournament
+ * partial-pivoting rounds on 256-row chunks chooses, their trailing updates
+ * on the tensor cores with FP64 accuracy (each operand row cut into seven
+ * 7-bit integer digits, digit products exact in FP32); each step's tournament
  * and pivot block run one step ahead on a second, library-owned stream of
  * the highest priority (one per device and host thread, made by the thread's
  * first call), forked from and joined back into `stream` with events; to
