@@ -618,11 +618,40 @@ __global__ void __launch_bounds__(256) apply_gather_kernel(double2* __restrict__
   }
 }
 
-__global__ void pad_identity_kernel(const double2* __restrict__ a, int n, double2* __restrict__ ap, int np) {
+// The inversion works on A 2^-e, e the exponent of max |Re|, |Im| over A
+// (exact scaling): its pivot thresholds are then relative and the FP32 pivot
+// choice stays in range.  amax holds the bits of that maximum (non-negative
+// doubles order like their bit patterns), set by amax_kernel after a clear.
+__device__ __forceinline__ int amax_exponent(const unsigned long long* amax) {
+  const double m = __longlong_as_double((long long)*amax);
+  int e = 0;
+  if (m > 0.0 && m <= 1.7976931348623157e308) frexp(m, &e);
+  return e;
+}
+
+__global__ void amax_kernel(const double2* __restrict__ a, size_t total, unsigned long long* __restrict__ amax) {
+  double m = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 z = a[e];
+    m = fmax(m, fmax(fabs(z.x), fabs(z.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void pad_identity_kernel(const double2* __restrict__ a, int n, double2* __restrict__ ap, int np,
+                                    const unsigned long long* __restrict__ amax) {
+  const int sh = -amax_exponent(amax);
   const size_t total = (size_t)np * np;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / np), j = (int)(e % np);
-    ap[e] = (i < n && j < n) ? a[(size_t)i * n + j] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+    if (i < n && j < n) {
+      const double2 z = a[(size_t)i * n + j];
+      ap[e] = make_double2(ldexp(z.x, sh), ldexp(z.y, sh));
+    } else {
+      ap[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
   }
 }
 
@@ -639,12 +668,16 @@ __global__ void swap_colmap_kernel(int n, const int* __restrict__ piv, int* __re
   }
 }
 
+// y = the inverse of A: the columns put back in order and the scale undone
+// (inv(A 2^-e) = 2^e inv(A))
 __global__ void unpermute_kernel(const double2* __restrict__ x, int np, int n, const int* __restrict__ inv,
-                                 double2* __restrict__ y) {
+                                 double2* __restrict__ y, const unsigned long long* __restrict__ amax) {
+  const int sh = -amax_exponent(amax);
   const size_t total = (size_t)n * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), c = (int)(e % n);
-    y[(size_t)i * n + inv[c]] = x[(size_t)i * np + c];
+    const double2 z = x[(size_t)i * np + c];
+    y[(size_t)i * n + inv[c]] = make_double2(ldexp(z.x, sh), ldexp(z.y, sh));
   }
 }
 
@@ -653,7 +686,8 @@ size_t pivot_inverse_workspace(int n) {
   const int nchunk = (n + kTourRows - 1) / kTourRows;
   return align256(sizeof(double2) * (size_t)np * np) + align256(sizeof(double2) * kTourNB * kTourNB) +
          2 * align256(sizeof(double2) * (size_t)kTourNB * np) + 2 * align256(sizeof(int) * (size_t)nchunk * kTourNB) +
-         2 * align256(sizeof(int) * (size_t)n) + align256(sizeof(int) * (1 + 4 * kTourNB)) + oz64_workspace(np);
+         2 * align256(sizeof(int) * (size_t)n) + align256(sizeof(int) * (1 + 4 * kTourNB)) + align256(8) +
+         oz64_workspace(np);
 }
 
 // Second stream (highest priority) and two events per device and host
@@ -714,6 +748,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   int* piv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
   int* inv = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (size_t)n);
   int* gather = reinterpret_cast<int*>(p); p += align256(sizeof(int) * (1 + 4 * kTourNB));
+  unsigned long long* amax = reinterpret_cast<unsigned long long*>(p); p += align256(8);
   void* ozws = p;
   LookAhead* la = nullptr;
   int rc = look_ahead(&la);
@@ -721,7 +756,15 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   const size_t total = (size_t)np * np;
   int bx = (int)((total + 255) / 256);
   if (bx > 152 * 8) bx = 152 * 8;
-  pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np);
+  NED_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned long long), st));
+  {
+    const size_t nn = (size_t)n * n;
+    int ab = (int)((nn + 255) / 256);
+    if (ab > 152 * 4) ab = 152 * 4;
+    amax_kernel<<<ab, 256, 0, st>>>(a, nn, amax);
+    NED_LAUNCH_CHECK("amax_kernel");
+  }
+  pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np, amax);
   NED_LAUNCH_CHECK("pad_identity_kernel");
   const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
   if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem))) return rc;
@@ -772,7 +815,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   NED_LAUNCH_CHECK("swap_colmap_kernel");
   int by = (int)(((size_t)n * n + 255) / 256);
   if (by > 152 * 8) by = 152 * 8;
-  unpermute_kernel<<<by, 256, 0, st>>>(ap, np, n, inv, a);
+  unpermute_kernel<<<by, 256, 0, st>>>(ap, np, n, inv, a, amax);
   NED_LAUNCH_CHECK("unpermute_kernel");
   return NEDMFT_OK;
 }

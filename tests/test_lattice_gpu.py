@@ -281,6 +281,36 @@ def test_impurity_update_needs_pivoting(args):
     assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
 
 
+@pytest.mark.parametrize("scale", [1e-24, 1e20])
+def test_impurity_update_at_large_and_small_scales(scale):
+    # G_loc scaled by 1e-24 or 1e20: the inversions see entries near 1e-24 and
+    # 1e24 (or 1e20), past the range where the tensor-core update applies its
+    # powers of two in FP32, and the pivoted inversion normalises the scale;
+    # G_imp matches the oracle to 1e-10 relative.  W Sigma W is compared at
+    # 1e20 only: at 1e-24 it is the difference of two matrices near 1e24,
+    # which leaves the oracle's own FP64 value at the level of its rounding.
+    args = (-2, 3, 0.05, 5.0, 0.25)  # N_c = 220
+    c = O.contour_grid(*args)
+    g = api.contour_grid(*args)
+    n = c.n_c
+    rng = np.random.default_rng(5)
+    base = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    gl = scale * np.roll(base, 1, axis=0).astype(np.complex128)
+    np.fill_diagonal(gl, 0.0)
+    sig = workload_sigma(c.t, c.w, 1.0, seed=3)
+    mo, mc = O.Model(U=1.0, E=1.0), api.make_model(1.0, 1.0)
+    s_ref, gi_ref = O.impurity_update(c, mo, gl, sig)
+    s_new, gimp = api.impurity_update(g, mc, torch.as_tensor(gl, device="cuda"), torch.as_tensor(sig, device="cuda"),
+                                      want_gimp=True)
+    torch.cuda.synchronize()
+    api.check_status()
+    w = c.w
+    sw = lambda s: w[:, None] * s * w[None, :]
+    if scale > 1.0:
+        assert rel(sw(s_new.cpu().numpy()), sw(s_ref)) < 1e-10
+    assert rel(gimp.cpu().numpy(), gi_ref) < 1e-10
+
+
 def test_impurity_update_from_two_host_threads_matches_sequential_calls():
     # each host thread gets its own look-ahead stream: two threads calling the
     # impurity step at once, each on its own stream, give bit for bit the
