@@ -104,12 +104,33 @@ struct Oz64Smem {
   static constexpr int kBytes = kA + kB + 1024 /*align*/ + 64 /*barriers*/;
 };
 
-// One CTA per output tile (128 rows, 64 real columns = 32 complex) of the
-// np x 2np real image of A.  Thread 0 brings the tile's 7 + 7 slice blocks in
-// with bulk copies, then issues the 28 products of order <= 6 (4 MMAs of
-// K = 16 each) into 7 order accumulators of 64 TMEM columns; 8 warps drain
-// them (one TMEM lane per row, two warps per lane quarter, 32 columns each).  Column j of A is written iff (wlo <= j <
-// whi) == inside (the look-ahead window: see pivot_inverse).
+// SMs left to the kernels of the look-ahead stream while the update runs (the
+// tournament's CTAs need more shared memory than an update CTA leaves free).
+constexpr int kOz64FreeSms = 8;
+
+// x as a double, exactly, on the integer units (IEEE 754 binary32 to binary64:
+// the exponent rebiased by 1023 - 127 = 896, the 23 fraction bits moved up by
+// 29); zero keeps its sign.  Subnormal, infinite and NaN values, which an order
+// sum scaled inside the FP32 range does not produce, take the conversion
+// instruction.  GB300 runs conversions on its two FP64 units per SM.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x), a = u & 0x7fffffffu;
+  if (a - 0x00800000u >= 0x7f000000u) {  // zero, subnormal, infinity or NaN
+    if (a == 0) return __hiloint2double((int)u, 0);
+    return (double)x;
+  }
+  return __hiloint2double((int)((u & 0x80000000u) | ((a >> 3) + (896u << 20))), (int)(u << 29));
+}
+
+// Persistent over the output tiles (128 rows, 64 real columns = 32 complex) of
+// the np x 2np real image of A, row-tile major, a contiguous run of tiles per
+// CTA, so consecutive tiles mostly share their 128 rows: the A slices are
+// brought in once per row tile.  Per tile thread 0 brings the 7 B (and, for a
+// new row tile, 7 A) slice blocks in with bulk copies, then issues the 28
+// products of order <= 6 (4 MMAs of K = 16 each) into 7 order accumulators of
+// 64 TMEM columns; 8 warps drain them (one TMEM lane per row, two warps per
+// lane quarter, 32 columns each).  Column j of A is written iff
+// (wlo <= j < whi) == inside (the look-ahead window: see pivot_inverse).
 __global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict__ A, int np, int k0,
                                                              const __nv_bfloat16* __restrict__ cimg,
                                                              const int* __restrict__ cexp,
@@ -124,12 +145,9 @@ __global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int mt = blockIdx.y, nt = blockIdx.x;  // 128-row tile, 64-column tile of the real image
-  const int n0 = nt * kOz64Bn;                 // first real column (2 j0)
-  // a tile wholly inside the skipped window: nothing to do
-  const int j_lo = n0 / 2, j_hi = j_lo + kOz64Bn / 2;
-  if (!inside && j_lo >= wlo && j_hi <= whi) return;
-  if (inside && (j_hi <= wlo || j_lo >= whi)) return;
+  const int ntn = 2 * np / kOz64Bn, ntiles = (np / 128) * ntn;
+  const int tile_lo = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+  const int tile_hi = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
   constexpr uint32_t kCols = 512;  // 7 x 64 columns, allocated as a power of two
   if (t == 0) {
     mbar_init(&bars[0], 1);
@@ -143,45 +161,72 @@ __global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const size_t cslice = (size_t)np * kOz64K, rslice = (size_t)2 * np * kOz64K;
-  if (t == 0) {
-    mbar_arrive_expect_tx(&bars[0], Oz64Smem::kA + Oz64Smem::kB);
+  // the next tile at or after `tile` that writes any column (or tile_hi)
+  auto next_active = [&](int tile) {
+    for (; tile < tile_hi; ++tile) {
+      const int j_lo = (tile % ntn) * (kOz64Bn / 2), j_hi = j_lo + kOz64Bn / 2;
+      const bool skip = inside ? (j_hi <= wlo || j_lo >= whi) : (j_lo >= wlo && j_hi <= whi);
+      if (!skip) break;
+    }
+    return tile;
+  };
+  int cur_mt = -1;  // the row tile whose A slices are (being) brought into shared memory
+  // thread 0: the operands of `tile` (the B slices, and the A slices of a new row tile) on bars[0]
+  auto load = [&](int tile) {
+    const int mt = tile / ntn, n0 = (tile % ntn) * kOz64Bn;
+    const bool load_a = mt != cur_mt;
+    cur_mt = mt;
+    if (t != 0) return;
+    mbar_arrive_expect_tx(&bars[0], (load_a ? Oz64Smem::kA : 0) + Oz64Smem::kB);
     for (int s = 0; s < kOz64S; ++s) {
       // the canonical image: 128-row tile mt of slice s (16 KB); 64 rows of
       // tile n0 / 128 starting at row n0 % 128 (8 KB, 8-row groups contiguous)
-      bulk_g2s(sa + s * kTileBytes, cimg + s * cslice + (size_t)mt * kTileElems, kTileBytes, &bars[0]);
-      bulk_g2s(sb + s * (kTileBytes / 2),
-               rimg + s * rslice + (size_t)(n0 >> 7) * kTileElems + (size_t)(n0 & 127) * 64, kTileBytes / 2,
-               &bars[0]);
+      if (load_a) bulk_g2s(sa + s * kTileBytes, cimg + s * cslice + (size_t)mt * kTileElems, kTileBytes, &bars[0]);
+      bulk_g2s(sb + s * (kTileBytes / 2), rimg + s * rslice + (size_t)(n0 >> 7) * kTileElems + (size_t)(n0 & 127) * 64,
+               kTileBytes / 2, &bars[0]);
     }
-  }
-  bool ok = __syncthreads_and(mbar_wait(&bars[0], 0, abort_flag));
-  if (ok && t == 0) {
-    tc_fence_after();
-    constexpr uint32_t idesc = idesc_bf16(128, kOz64Bn);
-    for (int a = 0; a < kOz64S; ++a)
-      for (int b = 0; a + b < kOz64Orders; ++b)
+  };
+  uint32_t it = 0;  // tiles done: the phase parity of both barriers
+  bool ok = true;
+  int tile = next_active(tile_lo);
+  if (tile < tile_hi) load(tile);
+  while (tile < tile_hi && ok) {
+    const int mt = tile / ntn, n0 = (tile % ntn) * kOz64Bn;  // 128-row tile, first real column (2 j0)
+    const uint32_t par = it & 1u;
+    ok = __syncthreads_and(mbar_wait(&bars[0], par, abort_flag));
+    if (ok && t == 0) {
+      tc_fence_after();
+      constexpr uint32_t idesc = idesc_bf16(128, kOz64Bn);
+      for (int a = 0; a < kOz64S; ++a)
+        for (int b = 0; a + b < kOz64Orders; ++b)
 #pragma unroll
-        for (int kk = 0; kk < kOz64K / 16; ++kk)
-          mma_bf16(tmem + (uint32_t)(a + b) * kOz64Bn, smem_desc(smem_u32(sa + a * kTileBytes) + kk * 256, 128, 1024),
-                   smem_desc(smem_u32(sb + b * (kTileBytes / 2)) + kk * 256, 128, 1024), idesc,
-                   (a > 0 || kk > 0) ? 1u : 0u);
-  }
-  if (t == 0) mma_commit(&bars[1]);  // after every product issued above (also after a failed load wait)
-  {
-    const uint64_t t0 = global_ns();
-    while (!mbar_test(&bars[1], 0) && global_ns() - t0 < kDrainNs) {
+          for (int kk = 0; kk < kOz64K / 16; ++kk)
+            mma_bf16(tmem + (uint32_t)(a + b) * kOz64Bn,
+                     smem_desc(smem_u32(sa + a * kTileBytes) + kk * 256, 128, 1024),
+                     smem_desc(smem_u32(sb + b * (kTileBytes / 2)) + kk * 256, 128, 1024), idesc,
+                     (a > 0 || kk > 0) ? 1u : 0u);
     }
-    // no copy may be left in flight at exit (only after a failed wait)
-    if (!ok && t == 0)
-      while (!mbar_test(&bars[0], 0) && global_ns() - t0 < kDrainNs) {
-      }
-  }
-  tc_fence_after();
-  if (ok) {
-    const int i = mt * 128 + (warp & 3) * 32 + lane;  // this thread's row (TMEM lane)
-    const bool ik = i >= k0 && i < k0 + 32;
-    const int ei = cexp[i];
+    if (t == 0) mma_commit(&bars[1]);  // after every product issued above (also after a failed load wait)
+    bool done;
     {
+      const uint64_t t0 = global_ns();
+      while (!(done = mbar_test(&bars[1], par)) && global_ns() - t0 < kDrainNs) {
+      }
+      // no copy may be left in flight at exit (only after a failed wait)
+      if (!ok && t == 0)
+        while (!mbar_test(&bars[0], par) && global_ns() - t0 < kDrainNs) {
+        }
+    }
+    if (!done) *abort_flag = 1;
+    ok = __syncthreads_and(ok && done);
+    tc_fence_after();
+    const int next = ok ? next_active(tile + 1) : tile_hi;
+    // the products have read the operands: the next tile's come in during this epilogue
+    if (next < tile_hi) load(next);
+    if (ok) {
+      const int i = mt * 128 + (warp & 3) * 32 + lane;  // this thread's row (TMEM lane)
+      const bool ik = i >= k0 && i < k0 + 32;
+      const int ei = cexp[i];
       const int c0 = 32 * (warp >> 2);  // warps 0-3 and 4-7 drain the two 32-column halves
       float hi[32], lo[32];
       tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0, hi);
@@ -198,6 +243,9 @@ __global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict
           lo[u] += e;
         }
       }
+      // the accumulators are read (ordered before the barrier after which the
+      // next tile's products overwrite them)
+      tc_fence_before();
 #pragma unroll
       for (int u = 0; u < 32; u += 2) {
         const int n = n0 + c0 + u, j = n >> 1;
@@ -205,24 +253,26 @@ __global__ void __launch_bounds__(256, 1) oz64_update_kernel(double2* __restrict
         const bool jk = j >= k0 && j < k0 + 32;
         // order sums carry 2^-7(o+2) 2^(ei + en): o is in the ldexpf above.
         // The power of two is applied in FP32 (exact) while the result stays
-        // well inside the FP32 range, else in FP64; then two conversions and
-        // two FP64 subtractions per value
+        // well inside the FP32 range, then two exact conversions on the
+        // integer units and two FP64 subtractions per value; else in FP64
         const int s0 = ei + rexp[n] - 2 * kOz64Bits, s1 = ei + rexp[n + 1] - 2 * kOz64Bits;
         double2* a = A + (size_t)i * np + j;
         double2 nv = (ik || jk) ? make_double2(0.0, 0.0) : *a;
         if (s0 > -64 && s0 < 64) {
-          nv.x = (nv.x - (double)ldexpf(hi[u], s0)) - (double)ldexpf(lo[u], s0);
+          nv.x = (nv.x - f32_to_f64(ldexpf(hi[u], s0))) - f32_to_f64(ldexpf(lo[u], s0));
         } else {
           nv.x -= ldexp((double)hi[u] + (double)lo[u], s0);
         }
         if (s1 > -64 && s1 < 64) {
-          nv.y = (nv.y - (double)ldexpf(hi[u + 1], s1)) - (double)ldexpf(lo[u + 1], s1);
+          nv.y = (nv.y - f32_to_f64(ldexpf(hi[u + 1], s1))) - f32_to_f64(ldexpf(lo[u + 1], s1));
         } else {
           nv.y -= ldexp((double)hi[u + 1] + (double)lo[u + 1], s1);
         }
         *a = nv;
       }
     }
+    ++it;
+    tile = next;
   }
   tc_fence_before();
   __syncthreads();
@@ -239,6 +289,14 @@ size_t oz64_workspace(int np) {
   return align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * np * kOz64K) +
          align256(sizeof(__nv_bfloat16) * (size_t)kOz64S * 2 * np * kOz64K) + align256(sizeof(int) * (size_t)np) +
          align256(sizeof(int) * (size_t)2 * np);
+}
+
+// Limit of the bounded waits of this file's kernel on the current device
+// (stream-ordered after earlier work on `st`).
+int oz64_set_wait_ns(uint64_t ns, cudaStream_t st) {
+  NED_CUDA(cudaMemcpyToSymbolAsync(umma::g_wait_ns, &ns, sizeof(ns), 0, cudaMemcpyHostToDevice, st));
+  NED_CUDA(cudaStreamSynchronize(st));
+  return NEDMFT_OK;
 }
 
 int oz64_prepare() {
@@ -259,8 +317,13 @@ int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* 
   oz64_pack_kernel<<<np / 8 + np / 32, 256, 0, st>>>(Rbuf, Cbuf, np, cimg, cexp, rimg, rexp);
   NED_LAUNCH_CHECK("oz64_pack_kernel");
   if (int rc = oz64_prepare()) return rc;
-  oz64_update_kernel<<<dim3(2 * np / kOz64Bn, np / 128), 256, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg,
-                                                                                      rexp, wlo, whi, inside, status);
+  int sms = 0;
+  if (int rc = device_sm_count(&sms)) return rc;
+  const int tiles = (np / 128) * (2 * np / kOz64Bn);
+  int grid = sms > 2 * kOz64FreeSms ? sms - kOz64FreeSms : sms;
+  if (grid > tiles) grid = tiles;
+  oz64_update_kernel<<<grid, 256, Oz64Smem::kBytes, st>>>(A, np, k0, cimg, cexp, rimg, rexp, wlo, whi, inside,
+                                                          status);
   NED_LAUNCH_CHECK("oz64_update_kernel");
   return NEDMFT_OK;
 }

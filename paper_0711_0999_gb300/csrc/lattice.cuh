@@ -36,6 +36,7 @@ int pivot_inverse_prepare();  // before capturing pivot_inverse into a graph
 // split); np a multiple of 128; columns j written iff (wlo <= j < whi) == inside.
 size_t oz64_workspace(int np);
 int oz64_prepare();  // sets the update kernel's shared-memory limit
+int oz64_set_wait_ns(uint64_t ns, cudaStream_t st);  // its bounded waits' limit on the current device
 int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* Cbuf, int wlo, int whi, bool inside,
                 void* ws, cudaStream_t st, int* status);
 

@@ -188,72 +188,74 @@ int launch_gj_small_fp64(const ContourDev& c, const ModelDev& m, const double* e
 //   P = inv(A_KK)                                        gj_pivot32_fp64_kernel
 //   R = P A_{K,:} with R_{:,K} = P;  C = A_{:,K} with C_K = -I   gj_panels_kernel
 //   A <- A(with rows K and columns K zeroed) - C R       gj_update_kernel
-// P = inv(A_KK) for the 32 x 32 FP64 block at (k0, k0) of every matrix: thread
-// t holds row t / 8, columns 4 (t % 8) .. +3 in registers; each step publishes
-// the pivot column, the pivot row and the pivot's inverse through
-// double-buffered shared arrays (written for step k + 1 while step k's are
-// still being read), so one barrier per step.  No pivoting: the caller orders
-// the rows.  Row r of the block is matrix row rows[r] when `rows` is given
-// and rows[r] >= 0 (the pivot rows of a step before they are swapped into
-// place), else k0 + r.
-__global__ void __launch_bounds__(256) gj_pivot32_fp64_kernel(const double2* __restrict__ A, int np, int k0,
-                                                              const int* __restrict__ rows,
-                                                              double2* __restrict__ Pbuf, int* status) {
-  __shared__ double2 colb[2][32], rowb[2][32], pinvb[2];
-  __shared__ int bad;
-  const int b = blockIdx.x, t = threadIdx.x;
-  const int r = t >> 3, c0 = 4 * (t & 7);
+// P = inv(A_KK) for the 32 x 32 FP64 block at (k0, k0) of every matrix, on a
+// cluster of kPivCtas CTAs per matrix: CTA q holds rows 4q .. 4q+3, one warp
+// per row, lane j its column j in registers, so the FP64 work of a step
+// spreads over eight SMs (GB300 has two FP64 FMA units per SM).  Each step
+// the warp of the next pivot row writes that row, and its lane on the
+// diagonal the pivot's inverse, into every CTA's double-buffered shared
+// arrays (written for step k + 1 while step k's are still being read), then
+// one cluster barrier per step.  A row's entry in the pivot column is its own
+// lane's value (a shuffle).  No pivoting: the caller orders the rows.  Row r
+// of the block is matrix row rows[r] when `rows` is given and rows[r] >= 0
+// (the pivot rows of a step before they are swapped into place), else k0 + r.
+constexpr int kPivCtas = 8;
+__device__ __forceinline__ void piv_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t piv_cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// store v at shared variable p of CTA `rank` of the cluster
+__device__ __forceinline__ void piv_st_remote(const double2* p, uint32_t rank, double2 v) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(a)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+__global__ void __cluster_dims__(kPivCtas, 1, 1) __launch_bounds__(128)
+    gj_pivot32_fp64_kernel(const double2* __restrict__ A, int np, int k0, const int* __restrict__ rows,
+                           double2* __restrict__ Pbuf, int* status) {
+  __shared__ __align__(16) double2 rowb[2][32];
+  __shared__ __align__(16) double2 pinvb[2];
+  const int b = blockIdx.x / kPivCtas;  // the matrix; clusters are consecutive CTAs
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = 4 * (int)piv_cluster_rank() + warp;
   const int src = (rows && rows[r] >= 0) ? rows[r] : k0 + r;
-  const double2* a = A + (size_t)b * np * np + (size_t)src * np + k0 + c0;
-  double2 v[4] = {a[0], a[1], a[2], a[3]};
-  if (t == 0) bad = 0;
+  double2 v = A[(size_t)b * np * np + (size_t)src * np + k0 + lane];
+  // step k's pivot row (warp-uniform branch) to every CTA
   auto publish = [&](int k, int buf) {
-    const int u = k & 3;  // register selects, not an indexed (local-memory) array
-    const double2 vk = u == 0 ? v[0] : (u == 1 ? v[1] : (u == 2 ? v[2] : v[3]));
-    if ((k >> 2) == (t & 7)) colb[buf][r] = vk;
-    if (r == k) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rowb[buf][c0 + q] = v[q];
-      if ((k >> 2) == (t & 7)) {
-        double2 pinv;
-        if (!cinv_guard<double>(vk, pinv, 1e-12)) bad = 1;
-        pinvb[buf] = pinv;
-      }
+    if (r != k) return;
+    double2 pinv = make_double2(0.0, 0.0);
+    if (lane == k && !cinv_guard<double>(v, pinv, 1e-12) && status) atomicCAS(status, 0, DS_SINGULAR);
+    for (uint32_t d = 0; d < (uint32_t)kPivCtas; ++d) {
+      piv_st_remote(&rowb[buf][lane], d, v);
+      if (lane == k) piv_st_remote(&pinvb[buf], d, pinv);
     }
   };
+  piv_cluster_sync();  // every CTA of the cluster runs before another writes its shared memory
   publish(0, 0);
-  __syncthreads();
-  const int lane = t & 31;
+  piv_cluster_sync();
   for (int k = 0; k < 32; ++k) {
     const int buf = k & 1;
     const double2 pinv = pinvb[buf];
-    // g = a_rk / a_kk once per row (the first of the row's 8 threads), shared
-    // by a shuffle: the FP64 units are the limit here
-    double2 g = make_double2(0.0, 0.0);
-    if ((t & 7) == 0) g = cmul(colb[buf][r], pinv);
-    g.x = __shfl_sync(0xffffffffu, g.x, lane & ~7);
-    g.y = __shfl_sync(0xffffffffu, g.y, lane & ~7);
     if (r == k) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = (c0 + u == k) ? pinv : cmul(v[u], pinv);
+      v = (lane == k) ? pinv : cmul(v, pinv);
     } else {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = c0 + u;
-        const double2 rb = rowb[buf][j];
-        // v - g rb in four FMAs
-        const double2 nv = make_double2(fma(-g.x, rb.x, fma(g.y, rb.y, v[u].x)),
-                                        fma(-g.x, rb.y, fma(-g.y, rb.x, v[u].y)));
-        v[u] = (j == k) ? make_double2(-g.x, -g.y) : nv;
-      }
+      const double2 rb = rowb[buf][lane];
+      const double2 ck = make_double2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k));
+      const double2 g = cmul(ck, pinv);  // a_rk / a_kk
+      // v - g rb in four FMAs
+      const double2 nv = make_double2(fma(-g.x, rb.x, fma(g.y, rb.y, v.x)), fma(-g.x, rb.y, fma(-g.y, rb.x, v.y)));
+      v = (lane == k) ? make_double2(-g.x, -g.y) : nv;
     }
     if (k + 1 < 32) publish(k + 1, buf ^ 1);
-    __syncthreads();
+    piv_cluster_sync();
   }
-  double2* out = Pbuf + (size_t)b * 32 * 32 + (size_t)r * 32 + c0;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = v[u];
-  if (t == 0 && bad && status) atomicCAS(status, 0, DS_SINGULAR);
+  Pbuf[(size_t)b * 32 * 32 + (size_t)r * 32 + lane] = v;
 }
 
 // W columns of R and W rows of C per CTA (W = 8 for one matrix: 4 x more
@@ -429,7 +431,7 @@ int gj_blocked_simt(cplx_t<T>* A, int n, int np, int nb_batch, cplx_t<T>* Pbuf, 
   if (int rc = ensure_dyn_smem(reinterpret_cast<const void*>(gj_update_kernel<NB>), (int)smem)) return rc;
   for (int k0 = 0; k0 < np; k0 += NB) {
     static_assert(NB == 32, "the pivot-block kernel inverts 32 x 32 blocks");
-    gj_pivot32_fp64_kernel<<<nb_batch, 256, 0, st>>>(A, np, k0, nullptr, Pbuf, status);
+    gj_pivot32_fp64_kernel<<<nb_batch * kPivCtas, 128, 0, st>>>(A, np, k0, nullptr, Pbuf, status);
     NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
     gj_panels_kernel<T, NB><<<dim3(np / 32, nb_batch), 256, 0, st>>>(A, np, k0, Pbuf, Rbuf, Cbuf);
     NED_LAUNCH_CHECK("gj_panels_kernel");
@@ -467,95 +469,98 @@ constexpr int kTourNB = 32;
 // swap sequence piv[k0 .. k0+31] (position k0 + j swaps with piv[k0 + j]),
 // and the same swaps as one gather of the <= 64 rows they move: gather[0] =
 // count, then pairs (position, row now at that position before the swaps).
+//
+// Thread t keeps candidate t's 32 panel entries in registers (the step loop
+// is unrolled, so every entry index is a constant).  Step j: the largest
+// |entry| of column j among the rows not yet chosen (ties: lower candidate
+// index) by a shuffle argmax per warp and a scan over the warps; the chosen
+// row's thread marks itself and puts its entries j .. 31 in shared memory;
+// every other row eliminates column j with it.  Rows do not move, so two
+// barriers per step; the winners are recorded in pivot order.
 __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restrict__ A, int np, int n, int k0,
                                                          const int* __restrict__ in, int in_count,
                                                          int* __restrict__ out, int final_round,
                                                          int* __restrict__ piv, int* __restrict__ gather,
                                                          int* status) {
-  extern __shared__ float2 tp[];  // kTourRows x (kTourNB + 1)
-  __shared__ int gidx[kTourRows];
-  constexpr int LD = kTourNB + 1;
-  const int c = blockIdx.x, t = threadIdx.x;
+  constexpr int kWarps = kTourRows / 32;
+  __shared__ float2 prow[2][kTourNB];     // the pivot row of a step (double-buffered by step)
+  __shared__ float wv[2][kWarps];         // per-warp maxima (double-buffered by step)
+  __shared__ int wi[2][kWarps];
+  __shared__ int win[kTourNB];            // the winners' rows, in pivot order (-1: none)
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
   const int i = c * kTourRows + t;
+  const int nrows = min(kTourRows, in_count - c * kTourRows);
   int row = -1;
   if (i < in_count) row = in ? in[i] : k0 + i;
-  gidx[t] = row;
   const int ncol = min(kTourNB, n - k0);
+  float2 v[kTourNB];
+#pragma unroll
   for (int j = 0; j < kTourNB; ++j) {
-    float2 v = make_float2(0.f, 0.f);
+    v[j] = make_float2(0.f, 0.f);
     if (row >= 0 && j < ncol) {
       const double2 z = A[(size_t)row * np + k0 + j];
-      v = make_float2((float)z.x, (float)z.y);
+      v[j] = make_float2((float)z.x, (float)z.y);
     }
-    tp[t * LD + j] = v;
+  }
+  bool live = row >= 0 && t < nrows;  // a candidate not chosen yet
+  const int steps = min(ncol, nrows);
+#pragma unroll
+  for (int j = 0; j < kTourNB; ++j) {
+    if (j < steps) {  // uniform over the block
+      const int sb = j & 1;
+      float m = live ? v[j].x * v[j].x + v[j].y * v[j].y : -1.f;
+      int idx = t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float om = __shfl_xor_sync(0xffffffffu, m, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (om > m || (om == m && oi < idx)) {
+          m = om;
+          idx = oi;
+        }
+      }
+      if (lane == 0) {
+        wv[sb][t >> 5] = m;
+        wi[sb][t >> 5] = idx;
+      }
+      __syncthreads();
+      float bm = wv[sb][0];
+      int p = wi[sb][0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w)
+        if (wv[sb][w] > bm || (wv[sb][w] == bm && wi[sb][w] < p)) {
+          bm = wv[sb][w];
+          p = wi[sb][w];
+        }
+      if (bm < 0.f) p = -1;  // no candidate left (not reached: a round has >= steps rows)
+      if (t == p) {
+        live = false;
+        win[j] = row;
+#pragma unroll
+        for (int cc = j; cc < kTourNB; ++cc) prow[sb][cc] = v[cc];
+      } else if (p < 0 && t == 0) {
+        win[j] = -1;
+      }
+      __syncthreads();
+      if (p >= 0 && live) {
+        const float2 pv = prow[sb][j];
+        const float pm = pv.x * pv.x + pv.y * pv.y;
+        if (pm > 0.f) {
+          const float2 pinv = make_float2(pv.x / pm, -pv.y / pm);
+          const float2 a = v[j];
+          const float2 f = make_float2(a.x * pinv.x - a.y * pinv.y, a.x * pinv.y + a.y * pinv.x);
+#pragma unroll
+          for (int cc = j + 1; cc < kTourNB; ++cc) {
+            const float2 r = prow[sb][cc];
+            v[cc].x -= f.x * r.x - f.y * r.y;
+            v[cc].y -= f.x * r.y + f.y * r.x;
+          }
+        }
+      }
+    }
   }
   __syncthreads();
-  const int nrows = min(kTourRows, in_count - c * kTourRows);
-  const int steps = min(ncol, nrows);
-  constexpr int kWarps = kTourRows / 32;
-  __shared__ float wv[kWarps];
-  __shared__ int wi[kWarps];
-  for (int j = 0; j < steps; ++j) {
-    // largest |entry| of column j among local rows >= j (ties: lower local
-    // index): a shuffle argmax per warp, then every thread over the warps
-    float m = -1.f;
-    if (t >= j && t < nrows && gidx[t] >= 0) {
-      const float2 v = tp[t * LD + j];
-      m = v.x * v.x + v.y * v.y;
-    }
-    int idx = t;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float om = __shfl_xor_sync(0xffffffffu, m, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (om > m || (om == m && oi < idx)) {
-        m = om;
-        idx = oi;
-      }
-    }
-    if ((t & 31) == 0) {
-      wv[t >> 5] = m;
-      wi[t >> 5] = idx;
-    }
-    __syncthreads();
-    float bm = wv[0];
-    int p = wi[0];
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w)
-      if (wv[w] > bm || (wv[w] == bm && wi[w] < p)) {
-        bm = wv[w];
-        p = wi[w];
-      }
-    // swap local rows j and p (one thread per column, one for the index)
-    if (p != j) {
-      if (t < kTourNB) {
-        const float2 x = tp[j * LD + t];
-        tp[j * LD + t] = tp[p * LD + t];
-        tp[p * LD + t] = x;
-      } else if (t == kTourNB) {
-        const int g = gidx[j];
-        gidx[j] = gidx[p];
-        gidx[p] = g;
-      }
-    }
-    __syncthreads();
-    const float2 pv = tp[j * LD + j];
-    const float pm = pv.x * pv.x + pv.y * pv.y;
-    if (t > j && t < nrows && pm > 0.f) {
-      const float2 pinv = make_float2(pv.x / pm, -pv.y / pm);
-      const float2 a = tp[t * LD + j];
-      const float2 f = make_float2(a.x * pinv.x - a.y * pinv.y, a.x * pinv.y + a.y * pinv.x);
-      for (int cc = j + 1; cc < kTourNB; ++cc) {
-        const float2 r = tp[j * LD + cc];
-        float2 v = tp[t * LD + cc];
-        v.x -= f.x * r.x - f.y * r.y;
-        v.y -= f.x * r.y + f.y * r.x;
-        tp[t * LD + cc] = v;
-      }
-    }
-    __syncthreads();
-  }
-  if (t < kTourNB) out[c * kTourNB + t] = (t < steps) ? gidx[t] : -1;
+  if (t < kTourNB) out[c * kTourNB + t] = (t < steps) ? win[t] : -1;
   if (final_round) {
     // winners -> swap sequence: position k0 + j takes the row now at the
     // winner's position.  The positions and rows involved (<= 64) get slots:
@@ -566,9 +571,9 @@ __global__ void __launch_bounds__(kTourRows) tour_kernel(const double2* __restri
     if (t < 2 * kTourNB) row_at[t] = where_at[t] = t;
     __syncthreads();
     if (t == 0) {
-      auto value = [&](int sl) { return sl < kTourNB ? k0 + sl : gidx[sl - kTourNB]; };
+      auto value = [&](int sl) { return sl < kTourNB ? k0 + sl : win[sl - kTourNB]; };
       for (int j = 0; j < kTourNB && k0 + j < n; ++j) {
-        const int w = j < steps ? gidx[j] : -1;
+        const int w = j < steps ? win[j] : -1;
         int target = k0 + j, tsl = j;
         if (w >= 0) {
           const int wsl = (w >= k0 && w < k0 + kTourNB) ? w - k0 : kTourNB + j;
@@ -722,8 +727,6 @@ int pivot_inverse_prepare() {
   LookAhead* la = nullptr;
   int rc = look_ahead(&la);
   if (!rc) rc = oz64_prepare();
-  if (!rc)
-    rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)(sizeof(float2) * kTourRows * (kTourNB + 1)));
   return rc;
 }
 
@@ -766,8 +769,6 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
   }
   pad_identity_kernel<<<bx, 256, 0, st>>>(a, n, ap, np, amax);
   NED_LAUNCH_CHECK("pad_identity_kernel");
-  const size_t tour_smem = sizeof(float2) * kTourRows * (kTourNB + 1);
-  if ((rc = ensure_dyn_smem(reinterpret_cast<const void*>(tour_kernel), (int)tour_smem))) return rc;
   // tournament over the rows k0 .. n-1 on the panel columns k0 .. k0+31, then
   // the inverse of the winners' 32 x 32 block (read in their rows, before the
   // swaps), on stream s
@@ -777,7 +778,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
     while (true) {
       const int blocks = (count + kTourRows - 1) / kTourRows;
       const int fin = blocks == 1;
-      tour_kernel<<<blocks, kTourRows, tour_smem, s>>>(ap, np, n, k0, in, count, cand[buf], fin, piv, gather,
+      tour_kernel<<<blocks, kTourRows, 0, s>>>(ap, np, n, k0, in, count, cand[buf], fin, piv, gather,
                                                        status);
       NED_LAUNCH_CHECK("tour_kernel");
       if (fin) break;
@@ -785,7 +786,7 @@ int pivot_inverse(double2* a, int n, void* ws, cudaStream_t st, int* status) {
       count = blocks * kTourNB;
       buf ^= 1;
     }
-    gj_pivot32_fp64_kernel<<<1, 256, 0, s>>>(ap, np, k0, cand[buf], pbuf, status);
+    gj_pivot32_fp64_kernel<<<kPivCtas, 128, 0, s>>>(ap, np, k0, cand[buf], pbuf, status);
     NED_LAUNCH_CHECK("gj_pivot32_fp64_kernel");
     return NEDMFT_OK;
   };

@@ -2310,12 +2310,13 @@ int umma_wait_selftest(int* status, cudaStream_t st) {
   return NEDMFT_OK;
 }
 
-// Limit of the bounded waits of this file's kernels on the current device
-// (stream-ordered after earlier work on `st`).
+// Limit of the bounded waits of the tensor-core kernels on the current device
+// (this file's and the impurity update's; stream-ordered after earlier work
+// on `st`).
 int umma_set_wait_ns(uint64_t ns, cudaStream_t st) {
   NED_CUDA(cudaMemcpyToSymbolAsync(umma::g_wait_ns, &ns, sizeof(ns), 0, cudaMemcpyHostToDevice, st));
   NED_CUDA(cudaStreamSynchronize(st));
-  return NEDMFT_OK;
+  return oz64_set_wait_ns(ns, st);
 }
 
 }  // namespace nedmft

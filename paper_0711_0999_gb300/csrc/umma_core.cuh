@@ -77,7 +77,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 // role aborted.  The waits at exit for copies and products already issued
 // (so that no copy lands in, and no product reads, a CTA that has left, and
 // the TMEM is idle when released) use the fixed kDrainNs.
-// (This header belongs to one translation unit, which owns g_wait_ns.)
+// (Every translation unit that includes this header has its own g_wait_ns;
+// nedmft_set_wait_limit sets each of them.)
 constexpr uint64_t kDrainNs = 2000000000ull;  // 2 s
 constexpr uint64_t kWaitDefaultNs = 2000000000ull;
 static __device__ uint64_t g_wait_ns = kWaitDefaultNs;
