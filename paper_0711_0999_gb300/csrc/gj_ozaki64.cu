@@ -299,7 +299,11 @@ int oz64_set_wait_ns(uint64_t ns, cudaStream_t st) {
   return NEDMFT_OK;
 }
 
+// The kernel's shared-memory limit and the device's SM count (which sizes its
+// grid), both cached per device: called before a graph capture of oz64_update.
 int oz64_prepare() {
+  int sms = 0;
+  if (int rc = device_sm_count(&sms)) return rc;
   return ensure_dyn_smem(reinterpret_cast<const void*>(oz64_update_kernel), Oz64Smem::kBytes);
 }
 

@@ -35,7 +35,7 @@ int pivot_inverse_prepare();  // before capturing pivot_inverse into a graph
 // FP64-accurate trailing update of pivot_inverse on the tensor cores (Ozaki
 // split); np a multiple of 128; columns j written iff (wlo <= j < whi) == inside.
 size_t oz64_workspace(int np);
-int oz64_prepare();  // sets the update kernel's shared-memory limit
+int oz64_prepare();  // the update kernel's shared-memory limit and the SM count, cached per device
 int oz64_set_wait_ns(uint64_t ns, cudaStream_t st);  // its bounded waits' limit on the current device
 int oz64_update(double2* A, int np, int k0, const double2* Rbuf, const double2* Cbuf, int wlo, int whi, bool inside,
                 void* ws, cudaStream_t st, int* status);
