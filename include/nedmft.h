@@ -361,7 +361,8 @@ size_t nedmft_impurity_workspace_size(const nedmft_contour* c);
  * 7-bit integer digits, digit products exact in FP32); each step's tournament
  * and pivot block run one step ahead on a second, library-owned stream of
  * the highest priority (one per device and host thread, made by the thread's
- * first call), forked from and joined back into `stream` with events; to
+ * first call and kept, with its two events, until the process ends), forked
+ * from and joined back into `stream` with events; to
  * capture the call into a CUDA graph, call it once outside the capture first
  * (nedmft_dmft_solve does so for its own graph).  gimp_d may be NULL;
  * if given, G_imp = inv(A0 - W sigma_new W) costs a third inversion.
