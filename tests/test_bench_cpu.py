@@ -87,6 +87,16 @@ def test_reference_arm_prints_the_contract_line():
                            "d2h_bytes_per_step": 0}
 
 
+def test_reference_arm_other_ranks_exit_without_work():
+    # under torchrun rank 0 alone times the oracle and prints; the others exit 0
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=120,
+                         cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == ""
+
+
 def test_default_held_out_pairs_take_one_pair_on_each_side_of_the_mott_transition():
     u_mott = 2 ** 0.5
     pairs = bench.held_out_pairs(16)
