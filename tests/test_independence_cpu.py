@@ -6,6 +6,7 @@ only by the smoke check and the benchmark's CPU-baseline / reference leg."""
 import ast
 import glob
 import os
+import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = "paper_0711_0999_gb300"
@@ -62,3 +63,17 @@ def test_oracle_reached_only_by_smoke_and_the_cpu_legs_of_the_benchmark():
         for mod, fn in imports(os.path.join(ROOT, name)):
             if mod.startswith("oracle"):
                 assert fn in fns, (name, mod, fn)
+
+
+def test_nothing_outside_the_scratch_folder_names_it():
+    # scratch work lives in a git-ignored folder; no source, test or script reads, imports or runs it
+    skip = {".git", "_work", "gpurun_out", "baseline", "__pycache__", "_build"}
+    hits = []
+    for base, dirs, files in os.walk(ROOT):
+        dirs[:] = [d for d in dirs if d not in skip]
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".sh", ".txt", ".cfg", ".toml", ".ini")):
+                path = os.path.join(base, f)
+                if re.search(r"(?<![A-Za-z0-9_])_work(?![A-Za-z0-9_])", open(path, errors="replace").read()):
+                    hits.append(os.path.relpath(path, ROOT))
+    assert hits == [os.path.join("tests", "test_independence_cpu.py")], hits
